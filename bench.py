@@ -1,0 +1,391 @@
+"""Throughput benchmark of the GF(4) BP decoder on the toric d = 15 workload.
+
+Workload (one "step"): the toric code d = 15 (450 qubits, 450 checks, 1800
+edges), i.i.d. depolarising noise at p = 0.02, 0.04, ..., 0.16 (8 values),
+10^6 shots per p (per rank), EWAInit-BP (alpha = 0.5), at most 100
+iterations, flooding schedule, fp32 messages: 8 decode launches, one per p.
+Syndromes are sampled on the device before timing (480 MB per rank, larger
+than the 129 MB L2, so no flush is needed between steps).
+
+Reported: shots/s and edge-updates/s of EWAInit-BP (the headline) and of
+plain/Momentum/AdaGrad BP on the same inputs, p50/p99 launch latency,
+the roofline of the decode kernel, an end-to-end figure through the C-ABI
+host-buffer entry point (bpq_decode_host), and the FP64 oracle timed on the
+host cores as a CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank decodes its own Philox shot range (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EWAInit-BP decoded shots/s & edge-updates/s vs plain kernel; p99 latency"
+P_SWEEP = [0.02, 0.04, 0.06, 0.08, 0.10, 0.12, 0.14, 0.16]
+SEED = 0xB9E00001
+CODE, DIST, MAX_ITER = "toric", 15, 100
+VARIANT_PARAMS = {"ewainit": dict(alpha=0.5), "plain": {}, "momentum": dict(alpha=0.5, gamma=0.0),
+                  "adagrad": dict(alpha=5.0)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shots-per-p", type=int, default=1_000_000)
+    ap.add_argument("--variants", default="ewainit,plain,momentum,adagrad")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {
+        "workload": f"toric d={DIST} (N=450, M=450, E=1800), depolarising p in {P_SWEEP}, "
+                    f"{args.shots_per_p} shots per p per rank, max_iter {MAX_ITER}, flooding schedule",
+        "code": f"toric d={DIST}", "p_sweep": P_SWEEP, "shots_per_p": args.shots_per_p,
+        "max_iter": MAX_ITER, "headline_variant": "ewainit alpha=0.5",
+        "l2": "inputs larger than L2 (syndromes 60 B/shot x 8e6 shots = 480 MB per rank); no flush",
+        "parallelism": f"replicas x{args.gpus}: disjoint Philox shot ranges, no data-path collective",
+        "seed": SEED,
+    }
+
+
+# ------------------------------------------------------------------ dist
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU baseline
+
+def cpu_baseline(args, seconds):
+    """The FP64 oracle, as it stands, on the host cores: rounds of `cores`
+    shots per p value (EWAInit-BP, the same seeds and shot indices as the GPU
+    run) until `seconds` of wall time have been spent."""
+    import oracle
+    from oracle import codes
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    H, _ = codes.build_code(CODE, DIST)
+    inputs = {}
+    for p in P_SWEEP:
+        inputs[p] = oracle.sample(H, *oracle.depolarizing(p), seed=SEED + P_SWEEP.index(p), shot0=0,
+                                  B=cores * 64)[1]
+    done, it_sum, rounds = 0, 0, 0
+    t0 = time.perf_counter()
+    while True:
+        for p in P_SWEEP:
+            prior = np.tile(np.asarray(oracle.depolarizing(p), dtype=np.float32).astype(np.float64), (H.shape[1], 1))
+            syn = inputs[p][rounds * cores:(rounds + 1) * cores]
+            _, _, iters = oracle.decode(H, syn, prior, "ewainit", max_iter=MAX_ITER, alpha=0.5, nthreads=cores)
+            done += syn.shape[0]
+            it_sum += int(iters.sum())
+        rounds += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (rounds + 1) * cores > cores * 64:
+            break
+    return {"value": done / el, "unit": "shots/s", "cores": cores, "kind": "oracle",
+            "edge_updates_per_s": it_sum * 1800 / el,
+            "sample": f"{rounds} rounds x {cores} shots x {len(P_SWEEP)} p values = {done} shots of the same "
+                      f"workload (EWAInit-BP, shot indices from 0), {el:.1f} s wall, FP64 oracle with "
+                      f"{cores} threads"}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(args, max(2.0, min(args.cpu_seconds, 20.0) / 2))
+        if s >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals) if vals else cb["value"]
+    line = {"metric": METRIC, "value": v, "unit": "shots/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": v, "unit": "shots/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2407_11523_gb300 as bpq
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    t = bpq.Tanner(CODE, DIST).upload()
+    B = args.shots_per_p
+    shot0 = rank * B
+    syns, priors = [], []
+    for k, p in enumerate(P_SWEEP):
+        _, syn = bpq.sample(t, *[p / 3] * 3, seed=SEED + k, shot0=shot0, B=B)
+        syns.append(syn)
+        priors.append(bpq.prior_tensor(t, p / 3, p / 3, p / 3))
+    del _
+    outs = [(torch.empty((B, t.N), dtype=torch.uint8, device=dev), torch.empty(B, dtype=torch.uint8, device=dev),
+             torch.empty(B, dtype=torch.uint8, device=dev)) for _ in P_SWEEP]
+    work = bpq.workspace(dev)
+    torch.cuda.synchronize()
+
+    results = {}
+    clocks = None
+    for v in args.variants.split(","):
+        params = bpq.make_params(v, **VARIANT_PARAMS[v])
+
+        def step(ev=None):
+            for k in range(len(P_SWEEP)):
+                if ev is not None:
+                    ev[k][0].record(stream)
+                bpq.decode(t, syns[k], priors[k], v, params=params, max_iter=MAX_ITER, out=outs[k], work=work)
+                if ev is not None:
+                    ev[k][1].record(stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        launch_ms = []
+        sampler = ClockSampler(dev.index) if v == "ewainit" else None
+        if sampler:
+            sampler.__enter__()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in P_SWEEP] for _ in range(args.steps)]
+        e0.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        if sampler:
+            sampler.__exit__()
+            clocks = sampler.summary()
+        ms = e0.elapsed_time(e1)
+        for s in range(args.steps):
+            for k in range(len(P_SWEEP)):
+                launch_ms.append(evs[s][k][0].elapsed_time(evs[s][k][1]))
+        iters_total = sum(int(o[2].sum(dtype=torch.int64).item()) for o in outs)
+        conv = sum(int(o[1].sum(dtype=torch.int64).item()) for o in outs)
+        sec = reduce_max(ms / 1e3, world)
+        shots = reduce_sum(float(B * len(P_SWEEP) * args.steps), world)
+        eu = reduce_sum(float(iters_total) * t.E * args.steps, world)
+        results[v] = {"shots_per_s": shots / sec, "edge_updates_per_s": eu / sec, "ms_per_step": sec * 1e3 / args.steps,
+                      "avg_iterations": iters_total / (B * len(P_SWEEP)), "converged_frac": conv / (B * len(P_SWEEP)),
+                      "launch_ms_mean": float(np.mean(launch_ms)), "launches": len(launch_ms),
+                      "edge_updates_per_step": iters_total * t.E}
+    head = results.get("ewainit") or next(iter(results.values()))
+
+    # p50/p99 launch latency at p = 0.08, EWAInit-BP, batches of 1 and 1024 shots
+    lat = {}
+    k8 = P_SWEEP.index(0.08)
+    params = bpq.make_params("ewainit", alpha=0.5)
+    for nb in (1, 1024):
+        sub = syns[k8][:nb].contiguous()
+        o = tuple(x[:nb] for x in outs[k8])
+        times = []
+        for r in range(230):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bpq.decode(t, sub, priors[k8], "ewainit", params=params, max_iter=MAX_ITER, out=o, work=work)
+            b.record(stream)
+            b.synchronize()
+            if r >= 30:
+                times.append(a.elapsed_time(b))
+        lat[f"batch_{nb}"] = {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
+                              "launches": len(times)}
+
+    # roofline of the decode kernel: SFU-bound in-SM arithmetic
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sfu_peak = bpq.probe_peak("sfu", blocks=sms * 8, threads=256, iters=4096)
+    fma_peak = bpq.probe_peak("fma", blocks=sms * 8, threads=256, iters=4096)
+    sfu_per_edge_update = 7.0
+    ew = results.get("ewainit", head)
+    kernel_sec = ew["launch_ms_mean"] / 1e3
+    achieved = sfu_per_edge_update * (ew["edge_updates_per_step"] / len(P_SWEEP)) / kernel_sec
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": sfu_peak / 1e12, "unit": "TSFUop/s",
+                "frac": achieved / sfu_peak, "traffic": None,
+                "kernel": "decode_kernel<EWAINIT>", "per_unit": f"{sfu_per_edge_update} SFU ops per edge-update",
+                "peak_source": "measured on this GPU by the MUFU.EX2 probe kernel (bpq_probe_peak)",
+                "fma_peak_tinst_per_s": fma_peak / 1e12, "sms": sms,
+                "hbm": {"algorithmic_bytes_per_shot": t.W * 4 + t.N + 2,
+                        "achieved_gbs": (t.W * 4 + t.N + 2) * args.shots_per_p / kernel_sec / 1e9}}
+
+    # end to end through bpq_decode_host with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        syn_h = [s.cpu().pin_memory() for s in syns]
+        pri_h = [p.cpu().pin_memory() for p in priors]
+        out_h = [(torch.empty((B, t.N), dtype=torch.uint8, pin_memory=True), torch.empty(B, dtype=torch.uint8, pin_memory=True),
+                  torch.empty(B, dtype=torch.uint8, pin_memory=True)) for _ in P_SWEEP]
+        dbuf = torch.empty(bpq.decode_host_bytes(t, B), dtype=torch.uint8, device=dev)
+        params = bpq.make_params("ewainit", alpha=0.5)
+
+        def hstep():
+            for k in range(len(P_SWEEP)):
+                bpq.decode_host(t, syn_h[k], pri_h[k], "ewainit", params=params, max_iter=MAX_ITER, out=out_h[k],
+                                dev_buf=dbuf)
+
+        for _ in range(args.warmup):
+            hstep()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        el = reduce_max(time.perf_counter() - t0, world)
+        shots = reduce_sum(float(B * len(P_SWEEP) * args.steps), world)
+        e2e = {"value": shots / el, "unit": "shots/s",
+               "h2d_bytes_per_step": len(P_SWEEP) * (B * t.W * 4 + t.N * 12),
+               "d2h_bytes_per_step": len(P_SWEEP) * B * (t.N + 2),
+               "api": "bpq_decode_host (C ABI, pinned host buffers, copies and a stream sync inside)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": head["shots_per_s"], "unit": "shots/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": workload_config(args),
+                "edge_updates_per_s": head["edge_updates_per_s"],
+                "variants": results, "vs_plain": (results["ewainit"]["shots_per_s"] / results["plain"]["shots_per_s"]
+                                                 if "plain" in results and "ewainit" in results else None),
+                "latency_ms": lat, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": len(P_SWEEP) * args.steps, "clocks": clocks,
+                "device": torch.cuda.get_device_name(dev)}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * bpq.h - C ABI of the GB300 (sm_103a) GF(4) belief-propagation decoder for
+ * surface codes: plain LLR-BP4, Momentum-BP, AdaGrad-BP and EWAInit-BP under
+ * the parallel (flooding) schedule, after "Improved Belief Propagation
+ * Decoding Algorithms for Surface Codes" (Chen, Yi, Liang, Wang).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: BPQ_OK (0) on success, a negative bpq_status otherwise.
+ *    bpq_last_error() then returns a message for the calling thread.
+ *  - Pointers named *_dev are device pointers owned by the caller (for
+ *    example torch tensors' data_ptr()); pointers named *_host are host
+ *    pointers owned by the caller.  The library never frees them.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  GPU entry
+ *    points only enqueue work on it and return; they do not synchronize,
+ *    except where a function says otherwise.
+ *  - Pauli codes: 0 = I, 1 = X, 2 = Y, 3 = Z.  Per-qubit probability and
+ *    LLR triples are ordered (X, Y, Z).
+ *  - Syndromes are bit-packed: shot b, check i is bit (i % 32) of the uint32
+ *    word syn[b * W + i / 32], W = ceil(M / 32).
+ *  - A non-converged shot is a normal result (converged = 0), not an error.
+ */
+#ifndef BPQ_H
+#define BPQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bpq_tanner bpq_tanner; /* opaque Tanner graph, library-owned */
+
+enum bpq_code { BPQ_PLANAR = 0, BPQ_TORIC = 1, BPQ_XZZX = 2 };
+
+/* Decoder variants: LLR-BP4 (Sec. II-B1), Momentum-BP (Sec. III-A1,
+ * Algorithm 1), AdaGrad-BP (Sec. III-A2), EWAInit-BP (Sec. III-B,
+ * Algorithm 2). */
+enum bpq_variant { BPQ_PLAIN = 0, BPQ_MOMENTUM = 1, BPQ_ADAGRAD = 2, BPQ_EWAINIT = 3 };
+
+enum bpq_status {
+    BPQ_OK = 0,
+    BPQ_EINVAL = -1,  /* bad argument (size, probability, null pointer, ...) */
+    BPQ_ENOMEM = -2,  /* host or device allocation failed */
+    BPQ_ECUDA = -3,   /* a CUDA runtime call failed */
+    BPQ_ESTATE = -4   /* handle not in the required state (e.g. not uploaded) */
+};
+
+/* Decoder parameters.
+ *   alpha: Momentum-BP learning rate (eq. (mombp2)); AdaGrad-BP boost rate
+ *          (eq. (boost)); EWAInit-BP discount factor (eq. (EWAInit)).
+ *          Unused by plain BP.
+ *   gamma: Momentum-BP decay (eq. (mombp1)); unused otherwise.
+ *   eps:   AdaGrad-BP epsilon of eq. (boost).
+ *   msg_clip: every check-to-variable and variable-to-check LLR message is
+ *          clipped to [-msg_clip, msg_clip] (the paper is silent on message
+ *          saturation; 30 by default).
+ *   adagrad_g_from_iter1: 1 = the squared-gradient sum G starts at t = 1
+ *          (g'(1) = -S(1)); 0 = G starts at t = 2.  Eq. (boost) applies from
+ *          t = 2 either way ("takes effect after the first iteration"). */
+typedef struct {
+    float alpha;
+    float gamma;
+    float eps;
+    float msg_clip;
+    int32_t adagrad_g_from_iter1;
+} bpq_params;
+
+/* Paper defaults for a variant (Sec. III-A2: AdaGrad alpha = 5; Sec. IV-A /
+ * Table I: Momentum gamma = 0, alpha = 0.5; EWAInit alpha = 0.5). */
+void bpq_default_params(int variant, bpq_params *out);
+
+/* ------------------------------------------------------------ Tanner graph */
+
+/* Build the check matrix of a surface code of distance d (2 <= d <= 32) on
+ * the host.  Planar: [[2d^2-2d+1, 1, d]]; toric: [[2d^2, 2, d]] (d >= 3);
+ * XZZX: the planar code with a Hadamard on the second hypergraph-product
+ * block (Sec. II-A; Sec. IV-B builds the codes as hypergraph products of
+ * repetition codes).  Qubit order: hypergraph-product block 1 (row-major
+ * d x d, toric) or (d x d, planar), then block 2; checks: X-type rows, then
+ * Z-type rows.  Does not touch the GPU.  *out must be released with
+ * bpq_free_tanner.  Errors: EINVAL for a bad code or d, ENOMEM. */
+int bpq_build_tanner(int code, int d, bpq_tanner **out);
+
+/* Build a Tanner graph from a dense M x N matrix of Pauli codes (row-major,
+ * host).  Every check and every qubit may have at most 4 non-identity
+ * entries (the decoder's padded degree); K is reported as -1 and no logical
+ * operators are known unless set with bpq_tanner_set_logicals.
+ * Errors: EINVAL (sizes, entries > 3, degree > 4, max(N, M) > 2048), ENOMEM. */
+int bpq_tanner_from_paulis(int M, int N, const uint8_t *H_host, bpq_tanner **out);
+
+/* Give a custom Tanner graph 2K logical operators (2K x N Pauli codes,
+ * host) for bpq_check_logical.  Must precede bpq_tanner_upload. */
+int bpq_tanner_set_logicals(bpq_tanner *t, int n_logicals, const uint8_t *L_host);
+
+/* Copy the graph's device tables to `device` (synchronous; allocates device
+ * memory owned by the handle).  Required before any GPU entry point.
+ * Errors: ECUDA, ENOMEM, ESTATE if already uploaded. */
+int bpq_tanner_upload(bpq_tanner *t, int device);
+
+/* Sizes: N qubits, M checks, E edges (non-identity entries), K logical
+ * qubits (-1 if unknown).  Any output pointer may be NULL. */
+int bpq_tanner_info(const bpq_tanner *t, int *N, int *M, int *E, int *K);
+
+/* Check-major CSR of the graph on the host: chk_ptr[M+1], chk_var[E],
+ * pauli[E]; edges of check i are chk_ptr[i] .. chk_ptr[i+1]-1 in increasing
+ * qubit order.  This is also the edge order of bpq_decode_trace. */
+int bpq_tanner_export(const bpq_tanner *t, int32_t *chk_ptr, int32_t *chk_var, uint8_t *pauli);
+
+/* The 2K logical operators used by bpq_check_logical (2K x N codes, host).
+ * Errors: ESTATE when none are known. */
+int bpq_tanner_logicals(const bpq_tanner *t, uint8_t *L_host);
+
+void bpq_free_tanner(bpq_tanner *t);
+
+/* ---------------------------------------------------------------- sampling */
+
+/* i.i.d. single-qubit Pauli channel (Sec. IV: depolarising p/3 each; the
+ * biased channel of Sec. IV-B3 likewise), shots shot0 .. shot0+B-1.
+ * Generator: Philox4x64-10 (Salmon et al., SC 2011), key (seed, 0), counter
+ * (shot, j / 4, 0, 0), word j % 4 is qubit j's draw u; u < floor(px 2^64)
+ * -> X, < floor((px+py) 2^64) -> Y, < floor((px+py+pz) 2^64) -> Z, else I
+ * (sums in double, in that order).  err_dev: B x N codes; syn_dev: B x W
+ * packed words, s_i = XOR_j <E_j, H_ij> (Sec. II-A).  Either output may be
+ * NULL only if B == 0.  Errors: EINVAL (px, py, pz < 0 or sum >= 1, B < 0),
+ * ESTATE, ECUDA. */
+int bpq_sample(const bpq_tanner *t, double px, double py, double pz, uint64_t seed, uint64_t shot0,
+               int B, uint8_t *err_dev, uint32_t *syn_dev, void *stream);
+
+/* ---------------------------------------------------------------- decoding */
+
+/* Bytes of device scratch that bpq_decode needs (a shot work queue and an
+ * error word); the caller allocates it, it need not be initialised, and
+ * concurrent decodes need separate scratch. */
+size_t bpq_decode_workspace_bytes(void);
+
+/* Decode B shots (Sec. II-B1 with the variant rules of Sec. III; flooding
+ * schedule, Algorithm 2's control flow for every variant):
+ *   prior LLR Pi = ln(p^I / p^W); m(0) = lambda(Pi) (eq. (init));
+ *   per iteration t = 1..max_iter: [EWAInit, t > 1: Pi(t) = alpha Pi(0) +
+ *   (1-alpha) Q(t-1)]; check-to-variable update (eq. (h_update)); posterior
+ *   Q (eq. (p_update) / (mombp1)-(mombp2) / (boost)); variable-to-check
+ *   update lambda_{H_ij}(Q - own anticommuting message) (eqs. (v_update),
+ *   (mombp5)); hard decision; stop as soon as <H, E^> = s.
+ * syn_dev: B x W packed syndromes.  prior_dev: N x 3 float probabilities
+ * (p^X, p^Y, p^Z) per qubit, each in (0, 1) with sum < 1, shared by all
+ * shots.  params: NULL = bpq_default_params(variant).  max_iter in
+ * [1, 255].  Outputs: est_dev B x N Pauli codes (the decision of the last
+ * iteration run), conv_dev B flags (1 = syndrome matched), iters_dev B
+ * iteration counts (1 .. max_iter).  work_dev: bpq_decode_workspace_bytes()
+ * of device scratch.  Shots are independent: any split of a batch gives the
+ * same per-shot results.  Errors: EINVAL, ESTATE, ECUDA; a device-side
+ * failure is reported by bpq_decode_status. */
+int bpq_decode(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+               const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
+               uint8_t *iters_dev, void *work_dev, void *stream);
+
+/* Synchronize `stream` and read the device error word a decode left in
+ * work_dev: 0 = no error; nonzero = a bounded wait inside the kernel gave up
+ * (the outputs of that launch are then invalid). */
+int bpq_decode_status(const void *work_dev, void *stream, int *device_error);
+
+/* bpq_decode with host buffers: copies syn_host (B x W words) and
+ * prior_host (N x 3) to the device, decodes, copies est/conv/iters back to
+ * the host buffers, and synchronizes `stream` before returning.  dev_buf is
+ * caller-owned device memory of at least bpq_decode_host_bytes(t, B) bytes.
+ * Host buffers should be pinned for the copies to run asynchronously. */
+size_t bpq_decode_host_bytes(const bpq_tanner *t, int B);
+int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host,
+                    int variant, const bpq_params *params, int max_iter, int B, uint8_t *est_host,
+                    uint8_t *conv_host, uint8_t *iters_host, void *dev_buf, size_t dev_buf_bytes,
+                    void *stream);
+
+/* Per-iteration record for parity checks (small B): runs exactly T
+ * iterations without the stopping rule and writes, in check-major edge
+ * order (bpq_tanner_export), m_v2c_dev [B][T+1][E] (t = 0 is eq. (init)),
+ * m_c2v_dev [B][T][E], Q_dev [B][T][N][3] and dec_dev [B][T][N].  Any
+ * record pointer may be NULL.  T in [1, 255]. */
+int bpq_decode_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
+                     int variant, const bpq_params *params, int T, int B, float *m_v2c_dev,
+                     float *m_c2v_dev, float *Q_dev, uint8_t *dec_dev, void *work_dev, void *stream);
+
+/* Launch shape of bpq_decode: threads per shot (a multiple of 32, at most
+ * 512, covering max(N, M) with at most 4 nodes per thread) and shots per
+ * CTA.  0 = let the library choose.  Stored in the handle. */
+int bpq_set_launch(bpq_tanner *t, int threads_per_shot, int shots_per_cta);
+int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_cta, int *ctas);
+
+/* ---------------------------------------------------------------- evaluation */
+
+/* Success criterion of Sec. IV: E^ in E S.  For each shot the residual
+ * R = E^ E (Pauli product, phase ignored) is classified: fail_dev[b] = 0 if R
+ * is a stabilizer, 1 if R anticommutes with some check (a detected error),
+ * 2 if R commutes with every check but anticommutes with a logical
+ * operator (an undetected error).  Errors: EINVAL, ESTATE (no logicals). */
+int bpq_check_logical(const bpq_tanner *t, const uint8_t *err_dev, const uint8_t *est_dev, int B,
+                      uint8_t *fail_dev, void *stream);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Throughput probe used to measure the roofline denominators on the running
+ * GPU (not part of the paper's method): launches `blocks` x `threads`
+ * threads, each running `iters` rounds of 8 independent chains of
+ * which = 0: MUFU ex2 (one SFU op per link), which = 1: fused multiply-add.
+ * Time it with events on `stream`; ops = blocks * threads * iters * 8.
+ * sink_dev: one float of device memory the kernel may write. */
+int bpq_probe_peak(int which, int blocks, int threads, int iters, float *sink_dev, void *stream);
+
+const char *bpq_last_error(void);
+int bpq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPQ_H */

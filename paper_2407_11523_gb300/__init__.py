@@ -1,0 +1,13 @@
+"""GB300-native GF(4) belief-propagation decoding of surface-code syndromes:
+plain LLR-BP4, Momentum-BP, AdaGrad-BP and EWAInit-BP under the flooding
+schedule (Chen, Yi, Liang, Wang, "Improved Belief Propagation Decoding
+Algorithms for Surface Codes").
+
+The compute lives in libbpq.so (CUDA for sm_103a, C ABI in include/bpq.h);
+this package is its thin Python binding.
+"""
+from ._binding import (  # noqa: F401
+    ADAGRAD, CODES, EWAINIT, MOMENTUM, PLAIN, PLANAR, TORIC, VARIANTS, XZZX,
+    BPQError, Params, Tanner, check_logical, decode, decode_host, decode_host_bytes, decode_status,
+    decode_trace, default_params, lib, make_params, prior_tensor, probe_peak, sample, workspace,
+)

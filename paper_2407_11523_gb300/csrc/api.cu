@@ -1,0 +1,447 @@
+// C-ABI entry points of libbpq (declared in include/bpq.h): device upload of
+// the Tanner graph, the Philox Pauli-channel sampler, argument checking and
+// launch of the decoder, the logical-failure classifier.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "bpq_internal.h"
+#include "decode_launch.h"
+
+using bpq::fail;
+
+namespace bpq {
+namespace {
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC 2011): 10 rounds of two 64x64->128 multiplications, Weyl key schedule.
+__device__ __forceinline__ void philox4x64_10(uint64_t &x0, uint64_t &x1, uint64_t &x2, uint64_t &x3,
+                                              uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
+        const uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
+        const uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+}
+
+__device__ __forceinline__ uint32_t anti_code(uint32_t a, uint32_t b) {
+    return (a != 0u) & (b != 0u) & (a != b);
+}
+
+// One thread per (shot, block of 4 qubits).
+__global__ void sample_errors_kernel(int N, int B, uint64_t seed, uint64_t shot0, uint64_t tx, uint64_t ty,
+                                     uint64_t tz, uint8_t *err) {
+    const int nblk = (N + 3) / 4;
+    const long total = (long)B * nblk;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const long b = idx / nblk;
+        const int blk = (int)(idx - b * nblk);
+        uint64_t x0 = shot0 + (uint64_t)b, x1 = (uint64_t)blk, x2 = 0, x3 = 0;
+        philox4x64_10(x0, x1, x2, x3, seed, 0);
+        const uint64_t u[4] = {x0, x1, x2, x3};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int j = 4 * blk + l;
+            if (j < N) err[b * N + j] = u[l] < tx ? 1 : u[l] < ty ? 2 : u[l] < tz ? 3 : 0;
+        }
+    }
+}
+
+// One warp per (shot, 32-check word); lane l computes check 32 w + l.
+__global__ void syndrome_kernel(const uint16_t *chk_slot, const uint8_t *chk_pauli, int N, int M, int W, int B,
+                                const uint8_t *err, uint32_t *syn) {
+    const long gw = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (long)B * W) return;
+    const long b = gw / W;
+    const int w = (int)(gw - b * W);
+    const int i = 32 * w + lane;
+    uint32_t bit = 0;
+    if (i < M) {
+        const uint32_t cp = chk_pauli[i];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const uint32_t sl = chk_slot[4 * i + n];
+            if (sl != kNoSlot) bit ^= anti_code(err[b * N + (sl >> 2)], (cp >> (2 * n)) & 3u);
+        }
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, bit);
+    if (lane == 0) syn[b * W + w] = word;
+}
+
+__device__ __forceinline__ uint32_t xbit(uint32_t c) { return (c == 1u) | (c == 2u); }
+__device__ __forceinline__ uint32_t zbit(uint32_t c) { return (c == 2u) | (c == 3u); }
+
+// One warp per shot: residual R = E^ E; 1 if R anticommutes with a check,
+// 2 if it commutes with all checks but not with all logical operators.
+__global__ void check_logical_kernel(const uint16_t *chk_slot, const uint8_t *chk_pauli, const uint8_t *logicals,
+                                     int nlog, int N, int M, int B, const uint8_t *err, const uint8_t *est,
+                                     uint8_t *fail_out) {
+    const long b = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    const uint8_t *e = err + b * N, *h = est + b * N;
+    uint32_t det = 0;
+    for (int i = lane; i < M; i += 32) {
+        const uint32_t cp = chk_pauli[i];
+        uint32_t par = 0;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const uint32_t sl = chk_slot[4 * i + n];
+            if (sl != kNoSlot) {
+                const int j = sl >> 2;
+                const uint32_t rx = xbit(e[j]) ^ xbit(h[j]), rz = zbit(e[j]) ^ zbit(h[j]);
+                const uint32_t p = (cp >> (2 * n)) & 3u;
+                par ^= (rx & zbit(p)) ^ (rz & xbit(p));
+            }
+        }
+        det |= par;
+    }
+    const bool detected = __any_sync(0xffffffffu, det) != 0;
+    bool logical = false;
+    if (!detected) {
+        for (int l = 0; l < nlog; ++l) {
+            uint32_t par = 0;
+            for (int j = lane; j < N; j += 32) {
+                const uint32_t rx = xbit(e[j]) ^ xbit(h[j]), rz = zbit(e[j]) ^ zbit(h[j]);
+                const uint32_t p = logicals[(size_t)l * N + j];
+                par ^= (rx & zbit(p)) ^ (rz & xbit(p));
+            }
+            const uint32_t odd = __popc(__ballot_sync(0xffffffffu, par)) & 1u;
+            if (odd) logical = true;
+        }
+    }
+    if (lane == 0) fail_out[b] = detected ? 1 : logical ? 2 : 0;
+}
+
+
+// Peak probes: `iters` rounds of 8 independent dependency chains per thread of
+// either MUFU.EX2 (x <- 2^-x, stays in [0.5, 1)) or FFMA.
+__global__ void probe_kernel(int which, int iters, float *sink) {
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 0.25f + 0.01f * k + 1e-6f * threadIdx.x;
+    if (which == 0) {
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(x[k]) : "f"(-x[k]));
+        }
+    } else {
+        const float a = 0.999f, b = 0.001f;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 12345.678f) sink[0] = s;  // keeps the chains live
+}
+
+uint64_t threshold(double c) {
+    if (c <= 0.0) return 0;
+    return (uint64_t)std::ldexp(c, 64);
+}
+
+int need_uploaded(const bpq_tanner *t) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    if (!t->dev_blob) return fail(BPQ_ESTATE, "tanner not uploaded to a device");
+    cudaError_t e = cudaSetDevice(t->device);
+    if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return BPQ_OK;
+}
+
+int cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return BPQ_OK;
+    return fail(BPQ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// The phi value that corresponds to the message clip: phi(c) = log1p(2 / expm1(c)).
+float phi_of_clip(float c) { return (float)std::log1p(2.0 / std::expm1((double)c)); }
+
+int check_params(int variant, const bpq_params *params, bpq_params *out) {
+    if (variant < BPQ_PLAIN || variant > BPQ_EWAINIT) return fail(BPQ_EINVAL, "unknown variant");
+    if (params) *out = *params;
+    else bpq_default_params(variant, out);
+    if (!(out->msg_clip > 0.0f && out->msg_clip <= 80.0f)) return fail(BPQ_EINVAL, "msg_clip must be in (0, 80]");
+    if (!std::isfinite(out->alpha) || !std::isfinite(out->gamma) || !std::isfinite(out->eps) || out->eps < 0.0f)
+        return fail(BPQ_EINVAL, "non-finite parameter");
+    return BPQ_OK;
+}
+
+int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prior, int variant,
+                     const bpq_params *params, int max_iter, int B, void *work, DecodeArgs &a) {
+    bpq_params p;
+    int rc = check_params(variant, params, &p);
+    if (rc) return rc;
+    if (B < 0) return fail(BPQ_EINVAL, "B < 0");
+    if (max_iter < 1 || max_iter > 255) return fail(BPQ_EINVAL, "max_iter must be in [1, 255]");
+    if (B > 0 && (!syn || !prior || !work)) return fail(BPQ_EINVAL, "NULL input or workspace");
+    std::memset(&a, 0, sizeof a);
+    a.table = t->d_table;
+    a.table_bytes = (uint32_t)t->table.size();
+    a.off_chk_pauli = t->off_chk_pauli;
+    a.off_var_pauli = t->off_var_pauli;
+    a.syn = syn;
+    a.prior = prior;
+    a.work = static_cast<uint32_t *>(work);
+    a.var_canon = t->d_var_canon;
+    a.chk_ptr = t->d_chk_ptr;
+    a.N = t->N;
+    a.M = t->M;
+    a.E = t->E;
+    a.W = (t->M + 31) / 32;
+    a.B = B;
+    a.max_iter = max_iter;
+    a.alpha = p.alpha;
+    a.gamma = p.gamma;
+    a.eps = p.eps;
+    a.clip = p.msg_clip;
+    a.phi_clip = phi_of_clip(p.msg_clip);
+    a.ada_from1 = p.adagrad_g_from_iter1 ? 1 : 0;
+    return BPQ_OK;
+}
+
+int launch_grid(long items, int per_block) {
+    long g = (items + per_block - 1) / per_block;
+    if (g > (1L << 30)) g = 1L << 30;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+}  // namespace bpq
+
+extern "C" {
+
+int bpq_tanner_upload(bpq_tanner *t, int device) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    if (t->dev_blob) return fail(BPQ_ESTATE, "tanner already uploaded");
+    int rc = bpq::cuda_check(cudaSetDevice(device), "cudaSetDevice");
+    if (rc) return rc;
+    int sms = 0;
+    rc = bpq::cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "SM count");
+    if (rc) return rc;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_tab = 0;
+    const size_t o_canon = al(t->table.size());
+    const size_t o_ptr = o_canon + al(sizeof(int32_t) * t->var_canon.size());
+    const size_t o_log = o_ptr + al(sizeof(int32_t) * t->chk_ptr.size());
+    const size_t total = o_log + al(t->logicals.size() + 1);
+    void *blob = nullptr;
+    rc = bpq::cuda_check(cudaMalloc(&blob, total), "cudaMalloc");
+    if (rc) return rc;
+    uint8_t *b = static_cast<uint8_t *>(blob);
+    cudaError_t e = cudaMemcpy(b + o_tab, t->table.data(), t->table.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + o_canon, t->var_canon.data(), sizeof(int32_t) * t->var_canon.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + o_ptr, t->chk_ptr.data(), sizeof(int32_t) * t->chk_ptr.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t->logicals.empty())
+        e = cudaMemcpy(b + o_log, t->logicals.data(), t->logicals.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(blob);
+        return bpq::cuda_check(e, "cudaMemcpy");
+    }
+    t->dev_blob = blob;
+    t->device = device;
+    t->num_sms = sms;
+    t->d_table = b + o_tab;
+    t->d_var_canon = reinterpret_cast<const int32_t *>(b + o_canon);
+    t->d_chk_ptr = reinterpret_cast<const int32_t *>(b + o_ptr);
+    t->d_logicals = t->logicals.empty() ? nullptr : b + o_log;
+    return BPQ_OK;
+}
+
+void bpq_free_tanner(bpq_tanner *t) {
+    if (!t) return;
+    if (t->dev_blob) {
+        cudaSetDevice(t->device);
+        cudaFree(t->dev_blob);
+    }
+    delete t;
+}
+
+int bpq_sample(const bpq_tanner *t, double px, double py, double pz, uint64_t seed, uint64_t shot0, int B,
+               uint8_t *err_dev, uint32_t *syn_dev, void *stream) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    if (B < 0) return fail(BPQ_EINVAL, "B < 0");
+    if (!(px >= 0 && py >= 0 && pz >= 0)) return fail(BPQ_EINVAL, "negative probability");
+    const double cx = px, cy = cx + py, cz = cy + pz;
+    if (!(cz < 1.0)) return fail(BPQ_EINVAL, "px + py + pz must be < 1");
+    if (B == 0) return BPQ_OK;
+    if (!err_dev || !syn_dev) return fail(BPQ_EINVAL, "NULL output");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nblk = (t->N + 3) / 4;
+    bpq::sample_errors_kernel<<<bpq::launch_grid((long)B * nblk, 256), 256, 0, st>>>(
+        t->N, B, seed, shot0, bpq::threshold(cx), bpq::threshold(cy), bpq::threshold(cz), err_dev);
+    const int W = (t->M + 31) / 32;
+    if (t->M > 0)
+        bpq::syndrome_kernel<<<bpq::launch_grid((long)B * W * 32, 256), 256, 0, st>>>(
+            reinterpret_cast<const uint16_t *>(t->d_table), t->d_table + t->off_chk_pauli, t->N, t->M, W, B, err_dev,
+            syn_dev);
+    return bpq::cuda_check(cudaGetLastError(), "sample launch");
+}
+
+size_t bpq_decode_workspace_bytes(void) { return bpq::kWorkspaceBytes; }
+
+int bpq_decode(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+               const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
+               uint8_t *iters_dev, void *work_dev, void *stream) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    bpq::DecodeArgs a;
+    rc = bpq::fill_decode_args(t, syn_dev, prior_dev, variant, params, max_iter, B, work_dev, a);
+    if (rc) return rc;
+    if (B == 0) return BPQ_OK;
+    if (!est_dev || !conv_dev || !iters_dev) return fail(BPQ_EINVAL, "NULL output");
+    a.est = est_dev;
+    a.conv = conv_dev;
+    a.iters = iters_dev;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = bpq::cuda_check(cudaMemsetAsync(work_dev, 0, 8, st), "workspace reset");
+    if (rc) return rc;
+    return bpq::decode_launch(t, a, variant, false, st, nullptr);
+}
+
+int bpq_decode_status(const void *work_dev, void *stream, int *device_error) {
+    if (!work_dev || !device_error) return fail(BPQ_EINVAL, "NULL argument");
+    uint32_t w[2] = {0, 0};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = bpq::cuda_check(cudaMemcpyAsync(w, work_dev, sizeof w, cudaMemcpyDeviceToHost, st), "status copy");
+    if (rc) return rc;
+    rc = bpq::cuda_check(cudaStreamSynchronize(st), "status sync");
+    if (rc) return rc;
+    *device_error = (int)w[1];
+    return BPQ_OK;
+}
+
+size_t bpq_decode_host_bytes(const bpq_tanner *t, int B) {
+    if (!t || B < 0) return 0;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t W = (t->M + 31) / 32;
+    return al(bpq::kWorkspaceBytes) + al(sizeof(uint32_t) * W * B) + al(sizeof(float) * 3 * t->N) +
+           al((size_t)B * t->N) + al(B) + al(B);
+}
+
+int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
+                    const bpq_params *params, int max_iter, int B, uint8_t *est_host, uint8_t *conv_host,
+                    uint8_t *iters_host, void *dev_buf, size_t dev_buf_bytes, void *stream) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    if (B < 0) return fail(BPQ_EINVAL, "B < 0");
+    if (B == 0) return BPQ_OK;
+    if (!syn_host || !prior_host || !est_host || !conv_host || !iters_host || !dev_buf)
+        return fail(BPQ_EINVAL, "NULL argument");
+    if (dev_buf_bytes < bpq_decode_host_bytes(t, B)) return fail(BPQ_EINVAL, "device buffer too small");
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t W = (t->M + 31) / 32;
+    uint8_t *p = static_cast<uint8_t *>(dev_buf);
+    void *work = p;
+    p += al(bpq::kWorkspaceBytes);
+    uint32_t *syn = reinterpret_cast<uint32_t *>(p);
+    p += al(sizeof(uint32_t) * W * B);
+    float *prior = reinterpret_cast<float *>(p);
+    p += al(sizeof(float) * 3 * t->N);
+    uint8_t *est = p;
+    p += al((size_t)B * t->N);
+    uint8_t *conv = p;
+    p += al(B);
+    uint8_t *iters = p;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = bpq::cuda_check(cudaMemcpyAsync(syn, syn_host, sizeof(uint32_t) * W * B, cudaMemcpyHostToDevice, st), "H2D");
+    if (rc) return rc;
+    rc = bpq::cuda_check(cudaMemcpyAsync(prior, prior_host, sizeof(float) * 3 * t->N, cudaMemcpyHostToDevice, st), "H2D");
+    if (rc) return rc;
+    rc = bpq_decode(t, syn, prior, variant, params, max_iter, B, est, conv, iters, work, stream);
+    if (rc) return rc;
+    rc = bpq::cuda_check(cudaMemcpyAsync(est_host, est, (size_t)B * t->N, cudaMemcpyDeviceToHost, st), "D2H");
+    if (rc) return rc;
+    rc = bpq::cuda_check(cudaMemcpyAsync(conv_host, conv, B, cudaMemcpyDeviceToHost, st), "D2H");
+    if (rc) return rc;
+    rc = bpq::cuda_check(cudaMemcpyAsync(iters_host, iters, B, cudaMemcpyDeviceToHost, st), "D2H");
+    if (rc) return rc;
+    return bpq::cuda_check(cudaStreamSynchronize(st), "stream sync");
+}
+
+int bpq_decode_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+                     const bpq_params *params, int T, int B, float *m_v2c_dev, float *m_c2v_dev, float *Q_dev,
+                     uint8_t *dec_dev, void *work_dev, void *stream) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    bpq::DecodeArgs a;
+    rc = bpq::fill_decode_args(t, syn_dev, prior_dev, variant, params, T, B, work_dev, a);
+    if (rc) return rc;
+    if (B == 0) return BPQ_OK;
+    a.tr_v2c = m_v2c_dev;
+    a.tr_c2v = m_c2v_dev;
+    a.tr_Q = Q_dev;
+    a.tr_dec = dec_dev;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc2 = bpq::cuda_check(cudaMemsetAsync(work_dev, 0, 8, st), "workspace reset");
+    if (rc2) return rc2;
+    return bpq::decode_launch(t, a, variant, true, st, nullptr);
+}
+
+int bpq_set_launch(bpq_tanner *t, int threads_per_shot, int shots_per_cta) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    if (threads_per_shot < 0 || shots_per_cta < 0 || shots_per_cta > 15) return fail(BPQ_EINVAL, "bad launch shape");
+    const int old_t = t->threads_per_shot, old_s = t->shots_per_cta;
+    t->threads_per_shot = threads_per_shot;
+    t->shots_per_cta = shots_per_cta;
+    bpq::LaunchShape s;
+    int rc = bpq::decode_launch_shape(t, &s);
+    if (rc) {
+        t->threads_per_shot = old_t;
+        t->shots_per_cta = old_s;
+    }
+    return rc;
+}
+
+int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_cta, int *ctas) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    bpq::LaunchShape s;
+    int rc = bpq::decode_launch_shape(t, &s);
+    if (rc) return rc;
+    if (threads_per_shot) *threads_per_shot = s.T;
+    if (shots_per_cta) *shots_per_cta = s.groups_per_cta;
+    if (ctas) *ctas = 0;
+    return BPQ_OK;
+}
+
+int bpq_probe_peak(int which, int blocks, int threads, int iters, float *sink_dev, void *stream) {
+    if (which < 0 || which > 1 || blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !sink_dev)
+        return fail(BPQ_EINVAL, "bad probe arguments");
+    bpq::probe_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(which, iters, sink_dev);
+    return bpq::cuda_check(cudaGetLastError(), "probe launch");
+}
+
+int bpq_check_logical(const bpq_tanner *t, const uint8_t *err_dev, const uint8_t *est_dev, int B, uint8_t *fail_dev,
+                      void *stream) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    if (B < 0) return fail(BPQ_EINVAL, "B < 0");
+    if (t->logicals.empty()) return fail(BPQ_ESTATE, "no logical operators known");
+    if (B == 0) return BPQ_OK;
+    if (!err_dev || !est_dev || !fail_dev) return fail(BPQ_EINVAL, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bpq::check_logical_kernel<<<bpq::launch_grid((long)B * 32, 256), 256, 0, st>>>(
+        reinterpret_cast<const uint16_t *>(t->d_table), t->d_table + t->off_chk_pauli, t->d_logicals,
+        (int)(t->logicals.size() / t->N), t->N, t->M, B, err_dev, est_dev, fail_dev);
+    return bpq::cuda_check(cudaGetLastError(), "check_logical launch");
+}
+
+}  // extern "C"

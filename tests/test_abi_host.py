@@ -1,0 +1,120 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every symbol include/bpq.h declares, builds the same Tanner graphs as the
+oracle's hypergraph-product construction, and rejects bad arguments."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from inputs import random_tree_code
+from oracle import codes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bpq():
+    import paper_2407_11523_gb300 as bpq
+    bpq.lib()
+    return bpq
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "bpq.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bpq_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(bpq):
+    L = bpq.lib()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    assert L.bpq_version() >= 100
+
+
+@pytest.mark.parametrize("kind", ["planar", "toric", "xzzx"])
+@pytest.mark.parametrize("d", [3, 4, 5, 7, 9, 15])
+def test_tanner_matches_oracle_construction(bpq, kind, d):
+    t = bpq.Tanner(kind, d)
+    H_oracle, K = codes.build_code(kind, d)
+    assert (t.M, t.N, t.K) == (H_oracle.shape[0], H_oracle.shape[1], K)
+    assert t.E == int((H_oracle != 0).sum())
+    ptr, var, pauli = t.export()
+    ii, jj, pp = oracle.edges(H_oracle)
+    assert (np.repeat(np.arange(t.M), np.diff(ptr)) == ii).all()
+    assert (var == jj).all() and (pauli == pp).all()
+
+
+@pytest.mark.parametrize("kind,d", [("planar", 3), ("planar", 7), ("toric", 4), ("toric", 6), ("xzzx", 5)])
+def test_library_logicals_are_valid(bpq, kind, d):
+    t = bpq.Tanner(kind, d)
+    H = t.dense()
+    Lg = t.logicals()
+    assert Lg.shape == (2 * t.K, t.N)
+    Hs, Ls = codes.to_symplectic(H), codes.to_symplectic(Lg)
+    assert not codes.symplectic_product(Ls, Hs).any()
+    group = codes.StabilizerGroup(H)
+    assert not group.contains(Lg).any()
+    assert codes.gf2_rank(codes.symplectic_product(Ls, Ls)) == 2 * t.K
+    # together with the checks they span a space of dimension N - K + 2K
+    assert codes.gf2_rank(np.vstack([Hs, Ls])) == t.N - t.K + 2 * t.K
+
+
+def test_custom_tanner_roundtrip(bpq):
+    H = random_tree_code(7, seed=3)
+    t = bpq.Tanner(H=H)
+    assert (t.dense() == H).all() and t.K == -1
+
+
+def test_rejects_bad_arguments(bpq):
+    with pytest.raises(bpq.BPQError):
+        bpq.Tanner("toric", 2)
+    with pytest.raises(bpq.BPQError):
+        bpq.Tanner("planar", 33)
+    with pytest.raises(bpq.BPQError):
+        bpq.Tanner(7, 5)
+    H = np.zeros((1, 6), dtype=np.uint8)
+    H[0, :5] = 1  # weight-5 check exceeds the padded degree
+    with pytest.raises(bpq.BPQError):
+        bpq.Tanner(H=H)
+    H = np.array([[4, 1]], dtype=np.uint8)
+    with pytest.raises(bpq.BPQError):
+        bpq.Tanner(H=H)
+    t = bpq.Tanner("planar", 5)
+    with pytest.raises(bpq.BPQError):
+        t.set_launch(48, 1)   # not a multiple of 32
+    with pytest.raises(bpq.BPQError):
+        bpq.Tanner("toric", 15).set_launch(32, 1)  # 450 nodes > 4 per thread x 32
+    # GPU entry points refuse a handle that was never uploaded, before any CUDA call
+    L = bpq.lib()
+    rc = L.bpq_decode(t.handle, None, None, 0, None, 10, 0, None, None, None, None, None)
+    assert rc == -4
+
+
+def test_launch_shapes(bpq):
+    t = bpq.Tanner("toric", 15)
+    assert t.launch() == (128, 4)
+    t.set_launch(256, 2)
+    assert t.launch() == (256, 2)
+    assert bpq.Tanner("planar", 5).launch()[0] == 32
+
+
+def test_default_params_follow_the_paper(bpq):
+    p = bpq.default_params("adagrad")
+    assert p.alpha == 5.0 and p.msg_clip == 30.0 and p.adagrad_g_from_iter1 == 1
+    p = bpq.default_params("momentum")
+    assert p.alpha == 0.5 and p.gamma == 0.0
+    assert bpq.default_params("ewainit").alpha == 0.5
+
+
+def test_workspace_and_host_buffer_sizes(bpq):
+    L = bpq.lib()
+    assert L.bpq_decode_workspace_bytes() >= 8
+    t = bpq.Tanner("toric", 15)
+    n = bpq.decode_host_bytes(t, 1000)
+    assert n >= 1000 * (t.N + 2) + 1000 * t.W * 4 + 3 * t.N * 4

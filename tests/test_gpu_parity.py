@@ -1,0 +1,226 @@
+"""Parity of the CUDA decoder with the FP64 oracle on identical inputs.
+
+Bars: variable-to-check and check-to-variable messages within 1e-4 absolute
+(log domain) for the first 5 iterations; final hard decisions equal on at
+least 99.9% of shots; logical error rates inside each other's 2-sigma
+binomial interval.  Launch-shape changes must not change any result."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from inputs import pack_bits, random_priors, random_syndromes, random_tree_code, trapping_set_code
+from oracle import codes
+
+pytestmark = pytest.mark.gpu
+
+MSG_TOL = 1e-4
+NTHREADS = os.cpu_count() or 4
+VARIANTS = ["plain", "momentum", "adagrad", "ewainit"]
+
+
+@pytest.fixture(scope="module")
+def bpq():
+    import paper_2407_11523_gb300 as bpq
+    assert torch.cuda.is_available()
+    return bpq
+
+
+def f32(prior):
+    """The float32 prior the GPU sees, widened for the oracle."""
+    return np.asarray(prior, dtype=np.float32).astype(np.float64)
+
+
+def gpu_inputs(bpq, t, syn_bits, prior):
+    syn = torch.from_numpy(pack_bits(syn_bits).view(np.int32)).cuda()
+    pri = torch.from_numpy(np.ascontiguousarray(prior, dtype=np.float32)).cuda()
+    return syn, pri
+
+
+def compare_trace(rec, H, syn_bits, prior, variant, T, shots, **kw):
+    worst = 0.0
+    for b in shots:
+        ref = oracle.trace(H, syn_bits[b], f32(prior), variant=variant, T=T, **kw)
+        d1 = np.abs(rec["m_v2c"][b] - ref["m_v2c"]).max()
+        d2 = np.abs(rec["m_c2v"][b] - ref["m_c2v"]).max()
+        worst = max(worst, d1, d2)
+        assert d1 <= MSG_TOL and d2 <= MSG_TOL, (variant, b, d1, d2)
+        q = np.abs(rec["Q"][b] - ref["Q"])
+        assert (q <= 4 * MSG_TOL + 1e-6 * np.abs(ref["Q"])).all(), (variant, b, q.max())
+    return worst
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_messages_planar_d5(bpq, variant):
+    t = bpq.Tanner("planar", 5)
+    H = t.dense()
+    ch = oracle.depolarizing(0.05)
+    _, s = oracle.sample(H, *ch, seed=0xB9E00000, shot0=0, B=600)
+    prior = np.tile(ch, (t.N, 1))
+    syn, pri = gpu_inputs(bpq, t, s, prior)
+    rec = bpq.decode_trace(t, syn, pri, variant=variant, T=5)
+    rec = {k: v.cpu().numpy() for k, v in rec.items()}
+    compare_trace(rec, H, s, prior, variant, 5, range(600))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_messages_toric_d15(bpq, variant):
+    t = bpq.Tanner("toric", 15)
+    H = t.dense()
+    ch = oracle.depolarizing(0.10)
+    _, s = oracle.sample(H, *ch, seed=0xB9E00001, shot0=1000, B=24)
+    prior = np.tile(ch, (t.N, 1))
+    syn, pri = gpu_inputs(bpq, t, s, prior)
+    rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5).items()}
+    compare_trace(rec, H, s, prior, variant, 5, range(24))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_messages_xzzx_biased_and_random_priors(bpq, variant):
+    t = bpq.Tanner("xzzx", 7)
+    H = t.dense()
+    ch = oracle.biased(0.08, 10.0)
+    _, s = oracle.sample(H, *ch, seed=17, shot0=0, B=40)
+    prior = random_priors(t.N, seed=4, lo=0.005, hi=0.1)
+    syn, pri = gpu_inputs(bpq, t, s, prior)
+    rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5).items()}
+    compare_trace(rec, H, s, prior, variant, 5, range(40))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_messages_trees_and_trapping_set(bpq, variant):
+    for seed in range(5):
+        H = random_tree_code(8, seed=700 + seed)
+        t = bpq.Tanner(H=H)
+        prior = random_priors(8, seed=800 + seed)
+        s = random_syndromes(H.shape[0], 8, seed=900 + seed)
+        syn, pri = gpu_inputs(bpq, t, s, prior)
+        rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5).items()}
+        compare_trace(rec, H, s, prior, variant, 5, range(8))
+    H = trapping_set_code()
+    t = bpq.Tanner(H=H)
+    s = np.array([[1, 0, 1, 0]], dtype=np.uint8)
+    prior = np.tile(oracle.depolarizing(0.01), (4, 1))
+    syn, pri = gpu_inputs(bpq, t, s, prior)
+    rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5).items()}
+    compare_trace(rec, H, s, prior, variant, 5, [0])
+
+
+def ler_interval(fails):
+    n = fails.size
+    p = fails.mean()
+    return p, 2 * np.sqrt(max(p * (1 - p), 1.0 / n) / n)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_decode_planar_d5_10k_shots(bpq, variant):
+    """The small configuration: planar d = 5, depolarising p = 0.05, 10^4
+    shots, at most 50 iterations."""
+    t = bpq.Tanner("planar", 5)
+    H = t.dense()
+    ch = oracle.depolarizing(0.05)
+    B = 10000
+    err_g, syn_g = bpq.sample(t, *ch, seed=0xB9E00000, shot0=0, B=B)
+    prior_g = bpq.prior_tensor(t, *ch)
+    est, conv, iters = bpq.decode(t, syn_g, prior_g, variant=variant, max_iter=50)
+    fail_g = bpq.check_logical(t, err_g, est)
+    torch.cuda.synchronize()
+    est, conv, iters, fail_g = (x.cpu().numpy() for x in (est, conv, iters, fail_g))
+
+    e_ref, s_ref = oracle.sample(H, *ch, seed=0xB9E00000, shot0=0, B=B)
+    prior = f32(np.tile(ch, (t.N, 1)))
+    est_r, conv_r, iters_r = oracle.decode(H, s_ref, prior, variant=variant, max_iter=50, nthreads=NTHREADS)
+    same = (est == est_r).all(axis=1)
+    assert same.mean() >= 0.999, (variant, same.mean())
+    assert (conv.astype(bool) == conv_r).mean() >= 0.999
+    fail_r, det_r = codes.logical_failure(H, e_ref, est_r)
+    pg, sg = ler_interval(fail_g > 0)
+    pr, sr = ler_interval(fail_r)
+    assert abs(pg - pr) <= max(sg, sr), (variant, pg, pr)
+    # internal consistency of the GPU outputs
+    assert ((iters >= 1) & (iters <= 50)).all() and (iters[conv == 0] == 50).all()
+    assert (fail_g[conv == 1] != 1).all() and (fail_g[conv == 0] == 1).all()
+
+
+def test_launch_shapes_give_identical_results(bpq):
+    t = bpq.Tanner("toric", 9)
+    ch = oracle.depolarizing(0.1)
+    _, syn = bpq.sample(t, *ch, seed=1, shot0=0, B=3000)
+    prior = bpq.prior_tensor(t, *ch)
+    outs = []
+    for shape in [(0, 0), (64, 3), (128, 2), (192, 1), (96, 4), (64, 1)]:
+        t.set_launch(*shape)
+        for v in VARIANTS:
+            outs.append((shape, v, bpq.decode(t, syn, prior, variant=v, max_iter=40)))
+    base = {v: o for s, v, o in outs if s == (0, 0)}
+    for s, v, o in outs:
+        for a, b in zip(o, base[v]):
+            assert torch.equal(a, b), (s, v)
+
+
+def test_shot_partition_invariance(bpq):
+    t = bpq.Tanner("planar", 9)
+    ch = oracle.depolarizing(0.08)
+    _, syn = bpq.sample(t, *ch, seed=2, shot0=0, B=2000)
+    prior = bpq.prior_tensor(t, *ch)
+    whole = bpq.decode(t, syn, prior, "ewainit", max_iter=100)
+    a = bpq.decode(t, syn[:777].contiguous(), prior, "ewainit", max_iter=100)
+    b = bpq.decode(t, syn[777:].contiguous(), prior, "ewainit", max_iter=100)
+    for w, x, y in zip(whole, a, b):
+        assert torch.equal(w, torch.cat([x, y]))
+
+
+def test_edge_cases(bpq):
+    t = bpq.Tanner("planar", 5)
+    prior = bpq.prior_tensor(t, *oracle.depolarizing(0.05))
+    # empty batch
+    syn = torch.zeros((0, t.W), dtype=torch.int32, device="cuda")
+    est, conv, iters = bpq.decode(t, syn, prior, "plain")
+    assert est.shape == (0, t.N)
+    # zero syndromes converge at the first iteration to the identity
+    syn = torch.zeros((5, t.W), dtype=torch.int32, device="cuda")
+    for v in VARIANTS:
+        est, conv, iters = bpq.decode(t, syn, prior, v)
+        assert (est == 0).all() and (conv == 1).all() and (iters == 1).all()
+    # max_iter = 1 and 255, one shot
+    _, syn = bpq.sample(t, *oracle.depolarizing(0.1), seed=4, shot0=0, B=1)
+    for mi in (1, 255):
+        est, conv, iters = bpq.decode(t, syn, prior, "plain", max_iter=mi)
+        assert 1 <= int(iters[0]) <= mi
+    with pytest.raises(bpq.BPQError):
+        bpq.decode(t, syn, prior, "plain", max_iter=0)
+    with pytest.raises(bpq.BPQError):
+        bpq.decode(t, syn, prior, "plain", max_iter=256)
+    # the device error word stays clear
+    work = bpq.workspace()
+    bpq.decode(t, syn, prior, "ewainit", work=work)
+    assert bpq.decode_status(work) == 0
+
+
+def test_trapping_set_parallel_never_converges_on_gpu(bpq):
+    """Table I, parallel column: LLR-BP4 and EWAInit-BP never converge on the
+    (4,0) trapping set with X errors on qubits 1 and 2 (prior 0.01, 50
+    iterations)."""
+    t = bpq.Tanner(H=trapping_set_code())
+    syn = torch.tensor([[0b0101]], dtype=torch.int32, device="cuda")
+    prior = bpq.prior_tensor(t, *oracle.depolarizing(0.01))
+    for v in ("plain", "ewainit"):
+        est, conv, iters = bpq.decode(t, syn, prior, v, max_iter=50)
+        assert int(conv[0]) == 0 and int(iters[0]) == 50
+        e = est[0].cpu().numpy()
+        assert (e == e[0]).all()
+
+
+def test_decode_host_matches_device(bpq):
+    t = bpq.Tanner("toric", 15)
+    ch = oracle.depolarizing(0.08)
+    _, syn = bpq.sample(t, *ch, seed=8, shot0=0, B=4096)
+    prior = bpq.prior_tensor(t, *ch)
+    dev = bpq.decode(t, syn, prior, "ewainit", max_iter=100)
+    syn_h = syn.cpu().pin_memory()
+    prior_h = prior.cpu().pin_memory()
+    host = bpq.decode_host(t, syn_h, prior_h, "ewainit", max_iter=100)
+    for a, b in zip(dev, host):
+        assert torch.equal(a.cpu(), b)
