@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
     return ap.parse_args()
 
 
@@ -298,7 +300,7 @@ def run_ours(args, rank, world):
     lat = {}
     k8 = P_SWEEP.index(0.08)
     params = bpq.make_params("ewainit", alpha=0.5)
-    for nb in (1, 1024):
+    for nb in (() if args.no_latency else (1, 1024)):
         sub = syns[k8][:nb].contiguous()
         o = tuple(x[:nb] for x in outs[k8])
         times = []
@@ -315,8 +317,8 @@ def run_ours(args, rank, world):
 
     # roofline of the decode kernel: SFU-bound in-SM arithmetic
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sfu_peak = bpq.probe_peak("sfu", blocks=sms * 8, threads=256, iters=4096)
-    fma_peak = bpq.probe_peak("fma", blocks=sms * 8, threads=256, iters=4096)
+    sfu_peak = float("nan") if args.no_probe else bpq.probe_peak("sfu", blocks=sms * 8, threads=256, iters=4096)
+    fma_peak = float("nan") if args.no_probe else bpq.probe_peak("fma", blocks=sms * 8, threads=256, iters=4096)
     sfu_per_edge_update = 7.0
     ew = results.get("ewainit", head)
     kernel_sec = ew["launch_ms_mean"] / 1e3
