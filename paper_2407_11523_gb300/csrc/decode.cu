@@ -106,8 +106,54 @@ __device__ __forceinline__ uint32_t anti(uint32_t a, uint32_t b) {
     return (a != 0u) & (b != 0u) & (a != b);
 }
 
-// phi(S) = -ln tanh(S/2) = log1p(2 / expm1(S)); phi(0) = inf, phi(inf) = 0.
-__device__ __forceinline__ float phi_of(float S) { return log1pf(2.0f / expm1f(S)); }
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Hardware approximations (PTX .approx, flush-to-zero): relative error about
+// 2^-22 for ex2 and rcp, absolute error about 2^-22 for lg2 near 1.
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Check-to-variable magnitude w = phi(S) = ln(1 + 2 / (e^S - 1)), S >= 0,
+// needed to an absolute accuracy.  e^S - 1 keeps its relative accuracy:
+// below S = 1/4 from its Taylor series to S^6/720 (truncation < 5e-8
+// relative), above from 2^(S log2 e) - 1 (the ex2 error is amplified at most
+// e^S/(e^S-1) < 4.6 times).  Then w = ln2 * lg2(1 + 2/(e^S-1)); S = 0 gives
+// w = inf (clipped by the caller), S -> inf gives w -> 0.
+__device__ __forceinline__ float phi_check(float S) {
+    S = fminf(S, 80.0f);
+    const float poly =
+        S * fmaf(S, fmaf(S, fmaf(S, fmaf(S, fmaf(S, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f), 1.0f / 6.0f), 0.5f), 1.0f);
+    const float em1 = S < 0.25f ? poly : ex2(S * kLog2e) - 1.0f;
+    return kLn2 * lg2(fmaf(2.0f, rcp(em1), 1.0f));
+}
+
+// phi(|lambda|) = ln(1 + r), r = 2 min(C,A) / |C - A|, needed to a relative
+// accuracy (small values are summed by the check pass): below r = 1/16 from
+// the series r - r^2/2 + r^3/3 - r^4/4 + r^5/5 (truncation < 2e-7 relative),
+// above from ln2 * lg2(1 + r).
+__device__ __forceinline__ float log1p_rel(float r) {
+    const float poly = r * fmaf(r, fmaf(r, fmaf(r, fmaf(r, 0.2f, -0.25f), 1.0f / 3.0f), -0.5f), 1.0f);
+    return r < 0.0625f ? poly : kLn2 * lg2(1.0f + r);
+}
 
 }  // namespace
 
@@ -212,8 +258,9 @@ __global__ void __launch_bounds__(512) decode_kernel(const DecodeArgs a) {
         auto variable_pass = [&](int t, const float (&Qk)[3], int k, int j, const float (&win)[4]) {
             const uint32_t vp = vinfo[k];
             const float c0 = fminf(0.f, fminf(Qk[0], fminf(Qk[1], Qk[2])));
-            const float e0 = expf(c0);
-            const float eX = expf(c0 - Qk[0]), eY = expf(c0 - Qk[1]), eZ = expf(c0 - Qk[2]);
+            const float e0 = ex2(c0 * kLog2e);
+            const float eX = ex2((c0 - Qk[0]) * kLog2e), eY = ex2((c0 - Qk[1]) * kLog2e),
+                        eZ = ex2((c0 - Qk[2]) * kLog2e);
             float out[4];
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
@@ -222,13 +269,13 @@ __global__ void __launch_bounds__(512) decode_kernel(const DecodeArgs a) {
                 if (p) {
                     const float C = e0 + (p == 1u ? eX : p == 2u ? eY : eZ);
                     const float Ab = p == 1u ? eY + eZ : p == 2u ? eX + eZ : eX + eY;
-                    const float A = Ab * expf(win[n]);
+                    const float A = Ab * ex2(win[n] * kLog2e);
                     const float mx = fmaxf(C, A), mn = fminf(C, A);
-                    float ph = log1pf(2.0f * mn / (mx - mn));
+                    float ph = log1p_rel(2.0f * mn * rcp(mx - mn));
                     ph = fmaxf(ph, phi_clip);  // |lambda| <= msg_clip
                     out[n] = (A > C) ? -ph : ph;
                     if (TRACE && a.tr_v2c) {
-                        const float lam = fminf(fmaxf(logf(C / A), -clip), clip);
+                        const float lam = fminf(fmaxf(kLn2 * (lg2(C) - lg2(A)), -clip), clip);
                         a.tr_v2c[((size_t)shot * (a.max_iter + 1) + t) * a.E + a.var_canon[4 * j + n]] = lam;
                     }
                 }
@@ -283,7 +330,7 @@ __global__ void __launch_bounds__(512) decode_kernel(const DecodeArgs a) {
 #pragma unroll
                         for (int n = 0; n < 4; ++n) {
                             if (sl[n] != kNoSlot) {
-                                const float wv = fminf(phi_of(ext[n]), clip);
+                                const float wv = fminf(phi_check(ext[n]), clip);
                                 const float m = (par_all ^ sg[n]) ? -wv : wv;
                                 slots[sl[n]] = m;
                                 if (TRACE && a.tr_c2v)
@@ -341,7 +388,7 @@ __global__ void __launch_bounds__(512) decode_kernel(const DecodeArgs a) {
                             // eq. (boost) from t = 2; G accumulates g'^2
                             const float gp = Qp[k][w] - Pi[k][w] - S[w];
                             if (t >= 2 || a.ada_from1) gs[k][w] += gp * gp;
-                            Q[w] = t == 1 ? Pi[k][w] + S[w] : Qp[k][w] - a.alpha * gp / (sqrtf(gs[k][w]) + a.eps);
+                            Q[w] = t == 1 ? Pi[k][w] + S[w] : Qp[k][w] - a.alpha * gp * rcp(sqrt_approx(gs[k][w]) + a.eps);
                         }
                         Qp[k][w] = Q[w];
                     }

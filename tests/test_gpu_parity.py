@@ -39,49 +39,49 @@ def gpu_inputs(bpq, t, syn_bits, prior):
     return syn, pri
 
 
-def ill_conditioned(H, syn_bits, prior, variant, T, shots, **kw):
-    """Shots whose oracle trajectory is itself unstable at the fp32 working
-    precision: perturbing each prior probability by 8 fp32 ulps (2^-20
-    relative; three sign patterns seeded by the shot index) moves some message
-    by more than half the tolerance.  Only AdaGrad-BP has such shots: where the
-    anticommuting check messages of a (qubit, Pauli) pair cancel, G is ~0 and
-    the step alpha g'/(sqrt(G)+eps) takes the sign of the rounding noise in g'."""
-    ill = set()
-    for b in shots:
-        rng = np.random.default_rng(1000 + b)
-        r0 = oracle.trace(H, syn_bits[b], f32(prior), variant=variant, T=T, **kw)
-        for _ in range(3):
-            pp = f32(prior) * (1 + 2.0 ** -20 * rng.choice([-1.0, 1.0], size=np.shape(prior)))
-            r1 = oracle.trace(H, syn_bits[b], pp, variant=variant, T=T, **kw)
-            d = max(np.abs(r0["m_v2c"] - r1["m_v2c"]).max(), np.abs(r0["m_c2v"] - r1["m_c2v"]).max())
-            if d > 0.5 * MSG_TOL:
-                ill.add(b)
-                break
-    return ill
-
-
-def compare_trace(rec, H, syn_bits, prior, variant, T, shots, skip=(), **kw):
+def oracle_sensitivity(H, syn_bits, prior, variant, T, b, **kw):
+    """Largest change of any oracle message when each prior probability is
+    perturbed by 8 fp32 ulps (2^-20 relative; three sign patterns seeded by
+    the shot index): the method's own sensitivity at the fp32 working
+    precision."""
+    rng = np.random.default_rng(1000 + b)
+    r0 = oracle.trace(H, syn_bits[b], f32(prior), variant=variant, T=T, **kw)
     worst = 0.0
-    checked = 0
+    for _ in range(3):
+        pp = f32(prior) * (1 + 2.0 ** -20 * rng.choice([-1.0, 1.0], size=np.shape(prior)))
+        r1 = oracle.trace(H, syn_bits[b], pp, variant=variant, T=T, **kw)
+        worst = max(worst, np.abs(r0["m_v2c"] - r1["m_v2c"]).max(), np.abs(r0["m_c2v"] - r1["m_c2v"]).max())
+    return worst
+
+
+def compare_trace(rec, H, syn_bits, prior, variant, T, shots, conditioned=False, **kw):
+    """Messages within MSG_TOL of the oracle.  With conditioned=True (used for
+    AdaGrad-BP only) a shot may deviate by MSG_TOL + 10 x the oracle's own
+    sensitivity: where the anticommuting check messages of a (qubit, Pauli)
+    pair cancel, G is ~0 and the boosted step alpha g'/(sqrt(G)+eps) takes the
+    sign of the rounding noise in g', so the method itself amplifies fp32
+    rounding.  Returns the number of shots inside the plain MSG_TOL bar."""
+    strict = 0
     for b in shots:
-        if b in skip:
-            continue
         ref = oracle.trace(H, syn_bits[b], f32(prior), variant=variant, T=T, **kw)
-        d1 = np.abs(rec["m_v2c"][b] - ref["m_v2c"]).max()
-        d2 = np.abs(rec["m_c2v"][b] - ref["m_c2v"]).max()
-        worst = max(worst, d1, d2)
-        assert d1 <= MSG_TOL and d2 <= MSG_TOL, (variant, b, d1, d2)
-        q = np.abs(rec["Q"][b] - ref["Q"])
-        assert (q <= 4 * MSG_TOL + 1e-6 * np.abs(ref["Q"])).all(), (variant, b, q.max())
-        checked += 1
-    return worst, checked
+        d = max(np.abs(rec["m_v2c"][b] - ref["m_v2c"]).max(), np.abs(rec["m_c2v"][b] - ref["m_c2v"]).max())
+        tol = MSG_TOL
+        if conditioned and d > MSG_TOL:
+            tol = MSG_TOL + 10.0 * oracle_sensitivity(H, syn_bits, prior, variant, T, b, **kw)
+        assert d <= tol, (variant, b, d, tol)
+        if d <= MSG_TOL:
+            strict += 1
+            q = np.abs(rec["Q"][b] - ref["Q"])
+            assert (q <= 4 * MSG_TOL + 1e-6 * np.abs(ref["Q"])).all(), (variant, b, q.max())
+    return strict
 
 
 def checked_trace(rec, H, syn_bits, prior, variant, T, shots, min_checked_frac=1.0, **kw):
-    skip = ill_conditioned(H, syn_bits, prior, variant, T, shots, **kw) if variant == "adagrad" else set()
-    worst, checked = compare_trace(rec, H, syn_bits, prior, variant, T, shots, skip=skip, **kw)
-    assert checked >= min_checked_frac * len(list(shots)), (variant, checked, len(skip))
-    return worst
+    shots = list(shots)
+    strict = compare_trace(rec, H, syn_bits, prior, variant, T, shots, conditioned=(variant == "adagrad"), **kw)
+    need = 1.0 if variant != "adagrad" else min_checked_frac
+    assert strict >= need * len(shots), (variant, strict, len(shots))
+    return strict
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -110,7 +110,7 @@ def test_messages_toric_d15(bpq, variant):
     if variant == "adagrad":
         # with eps = 1 the boosted step is well-conditioned: strict bar on every shot
         rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5, eps=1.0).items()}
-        compare_trace(rec, H, s, prior, variant, 5, range(24), eps=1.0)
+        assert compare_trace(rec, H, s, prior, variant, 5, range(24), eps=1.0) == 24
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
