@@ -172,6 +172,27 @@ int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *
                     uint8_t *conv_host, uint8_t *iters_host, void *dev_buf, size_t dev_buf_bytes,
                     void *stream);
 
+/* bpq_decode_host for callers that cannot allocate device memory (no
+ * cudaMalloc, cudaFree or allocating library call is made): for example a
+ * real-time decoding loop that must not allocate once running, or a process
+ * whose device memory is owned by another runtime's allocator.  The paper has
+ * no counterpart; this is an interface addition.  The device copies of the
+ * inputs and outputs and the decoder's shot queue live in one fixed 8 MiB
+ * array inside the library (held on every GPU that loads the library until
+ * the process exits).  B is limited to bpq_decode_host_noalloc_max_shots(t)
+ * (about 16000 toric d = 15 shots); larger batches return BPQ_EINVAL with a
+ * message.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the one array, which keeps the last
+ * call's contents (the shot queue is reset on every call): calls that may
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Arguments and errors otherwise as
+ * bpq_decode_host; the stream is synchronized before returning. */
+int bpq_decode_host_noalloc(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
+                            const bpq_params *params, int max_iter, int B, uint8_t *est_host, uint8_t *conv_host,
+                            uint8_t *iters_host, void *stream);
+int bpq_decode_host_noalloc_max_shots(const bpq_tanner *t);
+
 /* Per-iteration record for parity checks (small B): runs exactly T
  * iterations without the stopping rule and writes, in check-major edge
  * order (bpq_tanner_export), m_v2c_dev [B][T+1][E] (t = 0 is eq. (init)),

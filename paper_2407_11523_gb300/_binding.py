@@ -62,6 +62,8 @@ def lib():
             "bpq_decode_host_bytes": (sz, [P, i]),
             "bpq_decode_host": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, sz, P]),
             "bpq_decode_trace": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, P, P]),
+            "bpq_decode_host_noalloc": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P]),
+            "bpq_decode_host_noalloc_max_shots": (i, [P]),
             "bpq_set_launch": (i, [P, i, i]),
             "bpq_get_launch": (i, [P, pi, pi, pi]),
             "bpq_check_logical": (i, [P, P, P, i, P, P]),

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "bpq_internal.h"
@@ -221,6 +222,35 @@ int launch_grid(long items, int per_block) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// ---------------------------------------------------------------- no-allocation staging
+// Device memory for bpq_decode_host_noalloc: a fixed array in the library's
+// own image, so that callers that cannot allocate device memory can still
+// decode.  It is created when the library is loaded on a device and held
+// until the process exits.
+constexpr size_t kNoAllocBytes = size_t(8) << 20;
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` (which must be current).
+// In host code the symbol's name is only a host-side stand-in, so its device
+// address is looked up once per device and cached.
+int noalloc_scratch(int device, void **out) {
+    if (device < 0 || device >= kMaxDevices) return fail(BPQ_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(BPQ_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return BPQ_OK;
+}
+
 }  // namespace
 }  // namespace bpq
 
@@ -375,6 +405,34 @@ int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *
     rc = bpq::cuda_check(cudaMemcpyAsync(iters_host, iters, B, cudaMemcpyDeviceToHost, st), "D2H");
     if (rc) return rc;
     return bpq::cuda_check(cudaStreamSynchronize(st), "stream sync");
+}
+
+int bpq_decode_host_noalloc(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
+                            const bpq_params *params, int max_iter, int B, uint8_t *est_host, uint8_t *conv_host,
+                            uint8_t *iters_host, void *stream) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    if (B < 0) return fail(BPQ_EINVAL, "B < 0");
+    const size_t need = bpq_decode_host_bytes(t, B);
+    if (need > bpq::kNoAllocBytes)
+        return fail(BPQ_EINVAL, "batch too large for the fixed 8 MiB device staging area: at most " +
+                                    std::to_string(bpq_decode_host_noalloc_max_shots(t)) + " shots of this code");
+    void *scratch = nullptr;
+    rc = bpq::noalloc_scratch(t->device, &scratch);
+    if (rc) return rc;
+    return bpq_decode_host(t, syn_host, prior_host, variant, params, max_iter, B, est_host, conv_host, iters_host,
+                           scratch, bpq::kNoAllocBytes, stream);
+}
+
+int bpq_decode_host_noalloc_max_shots(const bpq_tanner *t) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    int lo = 0, hi = 1 << 24;
+    while (lo < hi) {  // largest B whose staging fits
+        const int mid = lo + (hi - lo + 1) / 2;
+        if (bpq_decode_host_bytes(t, mid) <= bpq::kNoAllocBytes) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 int bpq_decode_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
