@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve"],
+                    help="toric15: the headline sweep; mixed: many codes in one batched launch; "
+                         "serve: continuous-batching server on a Poisson request stream")
+    ap.add_argument("--loads", default="1e4,1e5,1e6,1e7", help="offered loads (requests/s) for --workload serve")
     return ap.parse_args()
 
 
@@ -81,6 +85,12 @@ def dist_setup(args):
             torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, world
+
+
+def shot_offset(rank, shots_per_p):
+    """First Philox shot index of a rank: ranks decode disjoint consecutive
+    shot ranges of every p value (weak scaling, no data-path collective)."""
+    return rank * shots_per_p
 
 
 def barrier(world):
@@ -205,19 +215,23 @@ def cpu_baseline(args, seconds):
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, each step a
+    bounded sample of the same workload (rank 0 only)."""
     if rank != 0:
         return
-    vals = []
+    vals, secs = [], []
     cb = None
     for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         cb = cpu_baseline(args, max(2.0, min(args.cpu_seconds, 20.0) / 2))
         if s >= args.warmup:
             vals.append(cb["value"])
+            secs.append(time.perf_counter() - t0)
     v = statistics.median(vals) if vals else cb["value"]
     line = {"metric": METRIC, "value": v, "unit": "shots/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": workload_config(args),
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs) if secs else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(args),
             "cpu_baseline": {"value": v, "unit": "shots/s", "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -235,7 +249,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     t = bpq.Tanner(CODE, DIST).upload()
     B = args.shots_per_p
-    shot0 = rank * B
+    shot0 = shot_offset(rank, B)
     syns, priors = [], []
     for k, p in enumerate(P_SWEEP):
         _, syn = bpq.sample(t, *[p / 3] * 3, seed=SEED + k, shot0=shot0, B=B)
@@ -377,11 +391,186 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+
+# ------------------------------------------------------------------ mixed-size batched workload
+
+MIX_CODES = [("planar", d) for d in (5, 9, 13, 17, 21, 25)] + [("toric", d) for d in (8, 12, 16)] + \
+    [("xzzx", d) for d in (7, 11, 15)]
+MIX_NOISE = [("depolarising p=0.06", (0.02, 0.02, 0.02)), ("Z-biased p=0.06 eta=10", (0.06 / 22, 0.06 / 22, 0.06 * 10 / 11))]
+MIX_TOTAL = 1 << 20
+
+
+def mixed_split(seed):
+    """Uneven split of 2^20 shots over the 24 (code, noise) groups: a
+    multinomial draw with Dirichlet(1) weights from a seeded generator."""
+    rng = np.random.default_rng(seed)
+    w = rng.dirichlet(np.ones(len(MIX_CODES) * len(MIX_NOISE)))
+    return rng.multinomial(MIX_TOTAL, w)
+
+
+def run_mixed(args, rank, world):
+    import torch
+
+    import paper_2407_11523_gb300 as bpq
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    counts = mixed_split(SEED)
+    tanners = {cd: bpq.Tanner(*cd).upload() for cd in MIX_CODES}
+    items, groups = [], []
+    k = 0
+    for cd in MIX_CODES:
+        for noise_name, ch in MIX_NOISE:
+            B = int(counts[k])
+            t = tanners[cd]
+            _, syn = bpq.sample(t, *ch, seed=SEED + 1000 + k, shot0=rank * MIX_TOTAL, B=B)
+            items.append((t, syn, bpq.prior_tensor(t, *ch)))
+            groups.append((cd, noise_name, B))
+            k += 1
+    params = bpq.make_params("ewainit", alpha=0.5)
+    # autotune each code's launch shape on its largest sample
+    shapes = {}
+    for cd in MIX_CODES:
+        t = tanners[cd]
+        best = max((it for it in items if it[0] is t), key=lambda it: it[1].shape[0])
+        sample = best[1][: min(8192, best[1].shape[0])].contiguous()
+        shapes[f"{cd[0]} d={cd[1]}"] = bpq.autotune(t, sample, best[2], "ewainit", params=params, max_iter=MAX_ITER)
+    work = bpq.workspace(dev)
+    outs = [(torch.empty((it[1].shape[0], it[0].N), dtype=torch.uint8, device=dev),
+             torch.empty(it[1].shape[0], dtype=torch.uint8, device=dev),
+             torch.empty(it[1].shape[0], dtype=torch.uint8, device=dev)) for it in items]
+
+    def per_code():
+        for (t, syn, prior), o in zip(items, outs):
+            if syn.shape[0]:
+                bpq.decode(t, syn, prior, "ewainit", params=params, max_iter=MAX_ITER, out=o, work=work)
+
+    plan = bpq.BatchPlan(items, "ewainit", params=params, max_iter=MAX_ITER)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.graph(graph, stream=side):
+        plan.run(stream=side)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return reduce_max(e0.elapsed_time(e1) / 1e3 / args.steps, world)
+
+    res = {}
+    res["per_code_launches"] = timed(per_code)
+    res["batched_launch"] = timed(lambda: plan.run())
+    res["batched_graph"] = timed(lambda: graph.replay())
+    # equal results, and the edge-updates of one pass
+    per_code()
+    ref = [tuple(x.clone() for x in o) for o in outs]
+    bat = plan.run()
+    torch.cuda.synchronize()
+    identical = all(torch.equal(a, b) for o, r in zip(bat, ref) for a, b in zip(o, r))
+    edge_updates = sum(int(o[2].sum(dtype=torch.int64).item()) * it[0].E for o, it in zip(ref, items))
+    errs = []
+    for (t, syn, prior), o, (cd, noise_name, B), k in zip(items, ref, groups, range(len(items))):
+        if B == 0:
+            errs.append(None)
+            continue
+        ch = MIX_NOISE[k % 2][1]
+        err, _ = bpq.sample(t, *ch, seed=SEED + 1000 + k, shot0=rank * MIX_TOTAL, B=B)
+        fail = bpq.check_logical(t, err, o[0])
+        errs.append(float((fail > 0).float().mean().item()))
+    shots = reduce_sum(float(MIX_TOTAL), world)
+    if rank == 0:
+        sec = res["batched_graph"]
+        line = {"metric": "batched mixed-size EWAInit-BP decoded shots/s (one persistent graph-captured launch)",
+                "value": shots / sec, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "planar d 5..25, toric d 8,12,16, XZZX d 7,11,15 x {depolarising, "
+                                       "Z-biased eta=10} at p=0.06; 2^20 shots split by a seeded multinomial; "
+                                       "EWAInit-BP alpha=0.5, max_iter 100",
+                           "groups": [{"code": f"{cd[0]} d={cd[1]}", "noise": nn, "shots": B, "ler": e}
+                                      for (cd, nn, B), e in zip(groups, errs)],
+                           "launch_shapes": shapes, "batch_plan": plan.info()},
+                "edge_updates_per_s": reduce_sum(float(edge_updates), world) / sec,
+                "compare_shots_per_s": {kk: shots / v for kk, v in res.items()},
+                "batched_equals_per_code": identical,
+                "gpu_launches": 1 * args.steps}
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ serving workload
+
+SERVE_CODES = [(k, d) for k in ("planar", "xzzx") for d in range(5, 32, 2)]
+
+
+def run_serve(args, rank, world):
+    import torch
+
+    import paper_2407_11523_gb300 as bpq
+
+    p = 0.05
+    ch = (p / 3, p / 3, p / 3)
+    codes = [bpq.Tanner(*cd).upload() for cd in SERVE_CODES]
+    priors = [bpq.prior_tensor(t, *ch) for t in codes]
+    params = bpq.make_params("ewainit", alpha=0.5)
+    srv = bpq.Server(codes, priors, "ewainit", params=params, max_iter=MAX_ITER, n_lanes=4, max_batch=4096)
+    rng = np.random.default_rng(SEED + 7)
+    pool = {}
+    R_pool = 20000
+    code_pool = rng.integers(0, len(codes), size=R_pool)
+    for c, t in enumerate(codes):
+        n = int((code_pool == c).sum())
+        _, syn = bpq.sample(t, *ch, seed=SEED + 2000 + c, shot0=rank * R_pool, B=max(n, 1))
+        pool[c] = syn.cpu().numpy().view(np.uint32)
+    fill = {c: 0 for c in pool}
+    syn_pool = []
+    for c in code_pool:
+        syn_pool.append(pool[c][fill[c]])
+        fill[c] += 1
+    results = []
+    srv.replay(code_pool[:2000], np.zeros(2000), syn_pool[:2000])  # warm-up
+    for load in [float(x) for x in args.loads.split(",")]:
+        R = int(min(R_pool, max(2000, load * 1.0)))
+        arrival = np.cumsum(rng.exponential(1.0 / load, size=R))
+        arrival -= arrival[0]
+        ests, conv, iters, done, used = srv.replay(code_pool[:R], arrival, syn_pool[:R])
+        lat = done - arrival
+        span = done.max() - arrival[0]
+        eu = sum(int(iters[r]) * codes[code_pool[r]].E for r in range(R))
+        results.append({"offered_per_s": load, "requests": R, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                        "p99_ms": float(np.percentile(lat, 99) * 1e3), "shots_per_s": R / span,
+                        "edge_updates_per_s": eu / span, "lanes_used": used,
+                        "converged_frac": float(conv.mean())})
+    if rank == 0:
+        best = max(r["shots_per_s"] for r in results)
+        line = {"metric": "serving: p50/p99 latency and shots/s under a Poisson request stream (continuous batching)",
+                "value": best, "unit": "shots/s", "n_gpus": world, "steps": len(results), "warmup": 1,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "single-shot requests, planar and XZZX codes d = 5, 7, ..., 31 (uniform), "
+                                       "depolarising p = 0.05, EWAInit-BP alpha = 0.5, max_iter 100; 4 lanes x 4096 "
+                                       "shots of device budget; Poisson arrivals",
+                           "loads": results},
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "mixed":
+        run_mixed(args, rank, world)
+    elif args.workload == "serve":
+        run_serve(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

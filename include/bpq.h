@@ -203,10 +203,100 @@ int bpq_decode_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *
                      float *m_c2v_dev, float *Q_dev, uint8_t *dec_dev, void *work_dev, void *stream);
 
 /* Launch shape of bpq_decode: threads per shot (a multiple of 32, at most
- * 512, covering max(N, M) with at most 4 nodes per thread) and shots per
- * CTA.  0 = let the library choose.  Stored in the handle. */
+ * 1024, covering max(N, M) with at most 2 nodes per thread, or at most 4 with
+ * at most 512 threads) and shots per CTA (at most 15, or 32 for one-warp
+ * shots).  0 = let the library choose (two nodes per thread, about 256
+ * threads per CTA).  Stored in the handle. */
 int bpq_set_launch(bpq_tanner *t, int threads_per_shot, int shots_per_cta);
 int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_cta, int *ctas);
+
+/* Autotuner of the launch shape (an addition; the paper has no GPU design):
+ * times bpq_decode on the caller's sample batch (same arguments as
+ * bpq_decode) for every candidate shape - 1..4 nodes per thread, 1..32
+ * shots per CTA - and stores the fastest in the
+ * handle (as bpq_set_launch would).  Synchronizes `stream`; the outputs are
+ * those of the last trial.  Reports the chosen shape and its time per
+ * launch (any output pointer may be NULL). */
+int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+                 const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
+                 uint8_t *iters_dev, void *work_dev, void *stream, int *threads_per_shot, int *shots_per_cta,
+                 float *best_ms);
+
+/* ---------------------------------------------------------------- batched decoding */
+
+/* Many codes in one persistent launch (an interface addition; the paper
+ * decodes one code at a time).  Each item is one code's batch: syndromes,
+ * prior and outputs exactly as for bpq_decode.  All items share the variant,
+ * parameters and max_iter.  The launch splits the items into tiles of
+ * (shots per CTA of that code) x tile_shots shots, queued code by code; a
+ * CTA of 512 threads decodes a tile with the code's own threads-per-shot
+ * (from bpq_set_launch / bpq_autotune, else the default) and re-stages the
+ * code's adjacency when the code changes.  Per-shot results equal those of
+ * bpq_decode bit for bit. */
+typedef struct {
+    const bpq_tanner *tanner;  /* uploaded; all items on one device */
+    const uint32_t *syn_dev;   /* [B][ceil(M/32)] */
+    const float *prior_dev;    /* [N][3] */
+    int B;
+    uint8_t *est_dev, *conv_dev, *iters_dev;
+} bpq_batch_item;
+
+typedef struct bpq_batch bpq_batch; /* opaque plan, library-owned */
+
+/* Device workspace needed by a plan of n_items items and total_shots shots. */
+size_t bpq_batch_workspace_bytes(int n_items, long total_shots, int tile_shots);
+
+/* Build the plan: per-code descriptors and the tile list, copied into
+ * work_dev (caller-owned, bpq_batch_workspace_bytes large, to stay untouched
+ * while the plan is used).  Synchronizes `stream`.  Errors: EINVAL, ESTATE,
+ * ECUDA.  Release with bpq_batch_free. */
+int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const bpq_params *params, int max_iter,
+                   int tile_shots, void *work_dev, size_t work_bytes, void *stream, bpq_batch **out);
+
+/* Enqueue one run of the plan on `stream` (a counter reset and one kernel
+ * launch; no host synchronization and no allocation, so the call can be
+ * captured in a CUDA graph).  Runs of one plan must not overlap. */
+int bpq_batch_launch(const bpq_batch *b, void *stream);
+
+int bpq_batch_info(const bpq_batch *b, int *ctas, int *tiles, int *npt_max, long *shots);
+void bpq_batch_free(bpq_batch *b);
+
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous-batching decoding server (an interface addition; the paper
+ * decodes offline batches).  n_lanes CUDA streams each own a slice of the
+ * caller's device memory for max_batch shots (the device-memory budget:
+ * at most n_lanes x max_batch shots are on the device at once).  Requests
+ * (one syndrome of one of the server's codes each) that have arrived wait
+ * in a FIFO; whenever a lane is free, all waiting requests up to max_batch
+ * are grouped by code and decoded there by one batched launch (see
+ * bpq_batch_plan), with their copies on the lane's stream, so requests that
+ * arrive while other lanes are busy run concurrently with them.  A
+ * request's result is the one bpq_decode gives for it alone. */
+typedef struct bpq_server bpq_server;
+
+size_t bpq_server_device_bytes(const bpq_tanner *const *codes, int n_codes, int n_lanes, int max_batch);
+
+/* codes: uploaded Tanner graphs on one device; priors_dev[c]: [N_c][3]
+ * float probabilities of code c.  Creates the lanes' streams, events and
+ * pinned host staging.  Errors: EINVAL, ESTATE, ECUDA. */
+int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors_dev, int n_codes, int variant,
+                      const bpq_params *params, int max_iter, int n_lanes, int max_batch, int tile_shots,
+                      void *dev_mem, size_t dev_bytes, bpq_server **out);
+
+/* Serve a request trace in real time (host wall clock from the call):
+ * request r is decoding code code[r], becomes available at arrival_s[r]
+ * seconds (non-decreasing), its packed syndrome is syn_host[syn_off[r] ..
+ * + ceil(M/32)), and its outputs go to est_host[est_off[r] .. + N],
+ * conv_host[r], iters_host[r].  done_s[r] receives the time at which the
+ * host saw the request's lane finish; latency = done_s - arrival_s.
+ * lanes_used (may be NULL): the largest number of lanes busy at once.
+ * Returns when every request is done. */
+int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *arrival_s, const uint32_t *syn_host,
+                      const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, uint8_t *conv_host,
+                      uint8_t *iters_host, double *done_s, int *lanes_used);
+
+void bpq_server_free(bpq_server *s);
 
 /* ---------------------------------------------------------------- evaluation */
 

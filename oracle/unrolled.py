@@ -1,0 +1,125 @@
+"""Oracle for the differentiable, unrolled EWAInit-BP decoder.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py): plain float64 PyTorch CPU
+code, differentiated by torch.autograd, used to check the CUDA forward and
+backward kernels.
+
+The model is EWAInit-BP (Sec. III-B, Algorithm 2) run for a fixed number T
+of flooding iterations, without the stopping rule, with three sets of
+trainable parameters added in the manner of neural BP (the paper's
+conclusion points to neural BP as a way to strengthen the algorithm):
+
+  * alpha_t, t = 1..T: the EWA weight of iteration t,
+        Pi^(t) = alpha_t Pi^(0) + (1 - alpha_t) Q^(t-1)      (t > 1; eq. (EWAInit));
+  * beta_t: damping of the variable-to-check messages,
+        m_v->c^(t) = (1 - beta_t) lambda(...) + beta_t m_v->c^(t-1);
+  * w_e: a weight on each check-to-variable message,
+        m_c->v^(t) = w_e (-1)^{s_i} 2 atanh(prod tanh(m_v->c^(t-1)/2))  (eq. (h_update)).
+
+With alpha_t = alpha, beta_t = 0 and w_e = 1 it is EWAInit-BP exactly.
+Messages are clipped to [-clip, clip] as in the decoder.  The loss is the
+cross-entropy of the final posterior against the true error, averaged over
+qubits and shots: per qubit the log-probabilities of (I, X, Y, Z) are
+log softmax(0, -Q_X, -Q_Y, -Q_Z), since Q_W = ln P(I)/P(W).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+
+def _anti(a, b):
+    return (a != 0) & (b != 0) & (a != b)
+
+
+class Graph:
+    """Check-major edge list of a Pauli check matrix and the index arrays the
+    vectorised forward needs."""
+
+    def __init__(self, H: np.ndarray):
+        H = np.asarray(H)
+        self.M, self.N = H.shape
+        ii, jj = np.nonzero(H)
+        self.E = ii.size
+        self.chk = torch.as_tensor(ii, dtype=torch.long)
+        self.var = torch.as_tensor(jj, dtype=torch.long)
+        self.pauli = torch.as_tensor(H[ii, jj].astype(np.int64))
+        # the other edges of the same check (padded with -1)
+        others = []
+        for e in range(self.E):
+            o = [f for f in np.nonzero(ii == ii[e])[0] if f != e]
+            others.append(o + [-1] * (3 - len(o)))
+        self.others = torch.as_tensor(np.array(others, dtype=np.int64))
+        # anticommutation of each edge with W = X, Y, Z: (E, 3)
+        self.anti = torch.as_tensor(np.stack([_anti(np.full(self.E, w), H[ii, jj]) for w in (1, 2, 3)], 1)
+                                    .astype(np.float64))
+        # one-hot of the commuting Pauli H of each edge: (E, 3)
+        self.own = torch.as_tensor(np.stack([H[ii, jj] == w for w in (1, 2, 3)], 1).astype(np.float64))
+
+
+def lam(q: torch.Tensor, own: torch.Tensor, anti: torch.Tensor) -> torch.Tensor:
+    """lambda_H(q) = ln((1 + e^{-q_H}) / sum_{W != H} e^{-q_W}), eq. (lambda);
+    q: (..., E, 3)."""
+    num = 1.0 + (torch.exp(-q) * own).sum(-1)
+    den = (torch.exp(-q) * anti).sum(-1)
+    return torch.log(num / den)
+
+
+def phi(x: torch.Tensor) -> torch.Tensor:
+    """phi(x) = -ln tanh(x/2) for x >= 0 (its own inverse)."""
+    return torch.log1p(2.0 / torch.expm1(x))
+
+
+def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0):
+    """Q^(T) (B, N, 3) of the unrolled decoder.  syn: (B, M) 0/1; prior:
+    (N, 3) probabilities; alpha, beta: (T,); w: (E,)."""
+    syn = torch.as_tensor(np.asarray(syn), dtype=torch.float64)
+    prior = torch.as_tensor(np.asarray(prior), dtype=torch.float64)
+    B = syn.shape[0]
+    pI = 1.0 - prior.sum(-1, keepdim=True)
+    Pi0 = torch.log(pI / prior)                                   # (N, 3)
+    sign = 1.0 - 2.0 * syn[:, g.chk]                              # (B, E): (-1)^{s_i}
+    v2c = lam(Pi0[g.var].expand(B, g.E, 3), g.own, g.anti).clamp(-clip, clip)   # eq. (init)
+    Qprev = Pi0.expand(B, g.N, 3)
+    Q = Qprev
+    for t in range(T):
+        Pit = Pi0 if t == 0 else alpha[t] * Pi0 + (1.0 - alpha[t]) * Qprev
+        # eq. (h_update): 2 atanh(prod_f tanh(m_f/2)) written with Gallager's
+        # identity  = prod_f sign(m_f) * phi(sum_f phi(|m_f|)),
+        # phi(x) = -ln tanh(x/2) = log1p(2/expm1(x)), which keeps full double
+        # accuracy near message saturation (the literal product loses ~1e-4
+        # there) and gives the stable derivative sinh(m_out)/sinh(m_f)
+        mag = phi(v2c.abs())
+        sgn = torch.sign(v2c)
+        mag_pad = torch.cat([mag, torch.zeros(B, 1, dtype=mag.dtype)], 1)         # index -1 -> phi = 0
+        sgn_pad = torch.cat([sgn, torch.ones(B, 1, dtype=sgn.dtype)], 1)
+        ext = mag_pad[:, g.others].sum(-1)                                         # (B, E)
+        psign = sgn_pad[:, g.others].prod(-1)
+        c2v = (w * sign * psign * phi(ext)).clamp(-clip, clip)
+        S = torch.zeros(B, g.N, 3, dtype=torch.float64).index_add(1, g.var, c2v[..., None] * g.anti)
+        Q = Pit.expand(B, g.N, 3) + S                                              # eq. (p_update)
+        q_own = Q[:, g.var, :] - c2v[..., None] * g.anti                           # Q minus own message
+        new = lam(q_own, g.own, g.anti).clamp(-clip, clip)
+        v2c = (1.0 - beta[t]) * new + beta[t] * v2c
+        Qprev = Q
+    return Q
+
+
+def loss(Q: torch.Tensor, err) -> torch.Tensor:
+    """Mean over shots and qubits of -log P(E_j = true Pauli), with
+    log P = log softmax(0, -Q_X, -Q_Y, -Q_Z)."""
+    err = torch.as_tensor(np.asarray(err), dtype=torch.long)
+    logits = torch.cat([torch.zeros_like(Q[..., :1]), -Q], -1)
+    logp = torch.log_softmax(logits, -1)
+    return -logp.gather(-1, err[..., None]).squeeze(-1).mean()
+
+
+def loss_and_grads(H, syn, err, prior, alpha, beta, w, T: int, clip: float = 30.0):
+    """(loss, d loss / d alpha, d beta, d w) in float64 by autograd."""
+    g = Graph(H)
+    a = torch.tensor(np.asarray(alpha, dtype=np.float64), requires_grad=True)
+    b = torch.tensor(np.asarray(beta, dtype=np.float64), requires_grad=True)
+    ww = torch.tensor(np.asarray(w, dtype=np.float64), requires_grad=True)
+    L = loss(forward(g, syn, prior, a, b, ww, T, clip), err)
+    L.backward()
+    return float(L), a.grad.numpy(), b.grad.numpy(), ww.grad.numpy()

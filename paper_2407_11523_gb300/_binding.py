@@ -65,9 +65,20 @@ def lib():
             "bpq_decode_host_noalloc": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P]),
             "bpq_decode_host_noalloc_max_shots": (i, [P]),
             "bpq_set_launch": (i, [P, i, i]),
+            "bpq_autotune": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, P, pi, pi,
+                                 ctypes.POINTER(ctypes.c_float)]),
             "bpq_get_launch": (i, [P, pi, pi, pi]),
             "bpq_check_logical": (i, [P, P, P, i, P, P]),
             "bpq_probe_peak": (i, [i, i, i, i, P, P]),
+            "bpq_batch_workspace_bytes": (sz, [i, ctypes.c_long, i]),
+            "bpq_batch_plan": (i, [P, i, i, ctypes.POINTER(Params), i, i, P, sz, P, PP]),
+            "bpq_batch_launch": (i, [P, P]),
+            "bpq_batch_info": (i, [P, pi, pi, pi, ctypes.POINTER(ctypes.c_long)]),
+            "bpq_batch_free": (None, [P]),
+            "bpq_server_device_bytes": (sz, [P, i, i, i]),
+            "bpq_server_create": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, i, P, sz, PP]),
+            "bpq_server_replay": (i, [P, i, P, P, P, P, P, P, P, P, P, pi]),
+            "bpq_server_free": (None, [P]),
             "bpq_last_error": (ctypes.c_char_p, []),
             "bpq_version": (i, []),
         }
@@ -187,6 +198,25 @@ class Tanner:
         t, s, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().bpq_get_launch(self._h, ctypes.byref(t), ctypes.byref(s), ctypes.byref(c)), "bpq_get_launch")
         return t.value, s.value
+
+
+def autotune(tanner: Tanner, syn, prior, variant="ewainit", params=None, max_iter=100, stream=None, **param_kw):
+    """Time every candidate launch shape on this sample batch and keep the
+    fastest in the handle; returns (threads_per_shot, shots_per_cta, ms)."""
+    tanner.upload()
+    v = VARIANTS.get(variant, variant)
+    p = params if params is not None else make_params(v, **param_kw)
+    B = syn.shape[0]
+    dev = syn.device
+    est = torch.empty((B, tanner.N), dtype=torch.uint8, device=dev)
+    conv = torch.empty(B, dtype=torch.uint8, device=dev)
+    iters = torch.empty(B, dtype=torch.uint8, device=dev)
+    work = workspace(dev)
+    t_, s_, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().bpq_autotune(tanner.handle, _ptr(syn), _ptr(prior), v, ctypes.byref(p), max_iter, B, _ptr(est),
+                              _ptr(conv), _ptr(iters), _ptr(work), _stream(stream), ctypes.byref(t_),
+                              ctypes.byref(s_), ctypes.byref(ms)), "bpq_autotune")
+    return t_.value, s_.value, ms.value
 
 
 def workspace(device=None) -> torch.Tensor:
@@ -313,3 +343,111 @@ def probe_peak(which: str, blocks: int, threads: int = 256, iters: int = 4096, s
     e1.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
     return blocks * threads * iters * 8 / sec
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("tanner", ctypes.c_void_p), ("syn_dev", ctypes.c_void_p), ("prior_dev", ctypes.c_void_p),
+                ("B", ctypes.c_int), ("est_dev", ctypes.c_void_p), ("conv_dev", ctypes.c_void_p),
+                ("iters_dev", ctypes.c_void_p)]
+
+
+class BatchPlan:
+    """Many codes decoded by one persistent launch (bpq_batch_*).
+
+    items: list of (Tanner, syndromes (B, W) int32, prior (N, 3) float32).
+    The plan owns its outputs (est, conv, iters per item) and its device
+    workspace; run() enqueues one launch (capturable in a CUDA graph)."""
+
+    def __init__(self, items, variant="ewainit", params=None, max_iter=100, tile_shots=64, stream=None,
+                 **param_kw):
+        v = VARIANTS.get(variant, variant)
+        self.params = params if params is not None else make_params(v, **param_kw)
+        self.tanners = [t.upload() for t, _, _ in items]
+        self.inputs = [(syn, prior) for _, syn, prior in items]
+        dev = items[0][1].device
+        self.outputs = []
+        arr = (BatchItem * len(items))()
+        total = 0
+        for k, (t, syn, prior) in enumerate(items):
+            B = syn.shape[0]
+            assert syn.is_contiguous() and prior.is_contiguous() and prior.dtype == torch.float32
+            out = (torch.empty((B, t.N), dtype=torch.uint8, device=dev), torch.empty(B, dtype=torch.uint8, device=dev),
+                   torch.empty(B, dtype=torch.uint8, device=dev))
+            self.outputs.append(out)
+            arr[k] = BatchItem(t.handle.value, syn.data_ptr(), prior.data_ptr(), B, out[0].data_ptr(),
+                               out[1].data_ptr(), out[2].data_ptr())
+            total += B
+        nbytes = lib().bpq_batch_workspace_bytes(len(items), total, tile_shots)
+        self.work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self._h = ctypes.c_void_p()
+        _check(lib().bpq_batch_plan(arr, len(items), v, ctypes.byref(self.params), max_iter, tile_shots,
+                                    _ptr(self.work), nbytes, _stream(stream), ctypes.byref(self._h)), "bpq_batch_plan")
+        self.total_shots = total
+
+    def run(self, stream=None):
+        _check(lib().bpq_batch_launch(self._h, _stream(stream)), "bpq_batch_launch")
+        return self.outputs
+
+    def info(self):
+        c, t, n, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_long()
+        _check(lib().bpq_batch_info(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(n), ctypes.byref(s)),
+               "bpq_batch_info")
+        return dict(ctas=c.value, tiles=t.value, npt_max=n.value, shots=s.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.bpq_batch_free(h)
+            self._h = None
+
+
+class Server:
+    """Continuous-batching decoding server (bpq_server_*): n_lanes streams
+    with room for max_batch shots each; replay() serves a request trace in
+    real time and returns per-request outputs and completion times."""
+
+    def __init__(self, codes, priors, variant="ewainit", params=None, max_iter=100, n_lanes=4, max_batch=4096,
+                 tile_shots=16, **param_kw):
+        v = VARIANTS.get(variant, variant)
+        self.params = params if params is not None else make_params(v, **param_kw)
+        self.codes = [t.upload() for t in codes]
+        self.priors = [p.contiguous() for p in priors]
+        n = len(codes)
+        harr = (ctypes.c_void_p * n)(*[t.handle.value for t in self.codes])
+        parr = (ctypes.c_void_p * n)(*[p.data_ptr() for p in self.priors])
+        nbytes = lib().bpq_server_device_bytes(harr, n, n_lanes, max_batch)
+        self.mem = torch.empty(nbytes, dtype=torch.uint8, device=self.priors[0].device)
+        self._h = ctypes.c_void_p()
+        _check(lib().bpq_server_create(harr, parr, n, v, ctypes.byref(self.params), max_iter, n_lanes, max_batch,
+                                       tile_shots, _ptr(self.mem), nbytes, ctypes.byref(self._h)), "bpq_server_create")
+
+    def replay(self, code, arrival_s, syn_list):
+        """code: (R,) int; arrival_s: (R,) float, non-decreasing; syn_list:
+        packed syndrome words (uint32 numpy) of each request.  Returns
+        (est list, conv (R,), iters (R,), done_s (R,), lanes_used)."""
+        code = np.ascontiguousarray(code, dtype=np.int32)
+        arrival = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        R = code.size
+        syn_off = np.zeros(R, dtype=np.int64)
+        est_off = np.zeros(R, dtype=np.int64)
+        Ns = [self.codes[c].N for c in code]
+        lens = [len(x) for x in syn_list]
+        syn_off[1:] = np.cumsum(lens)[:-1]
+        est_off[1:] = np.cumsum(Ns)[:-1]
+        syn = np.ascontiguousarray(np.concatenate(syn_list).astype(np.uint32)) if R else np.zeros(1, np.uint32)
+        est = np.zeros(max(1, int(sum(Ns))), dtype=np.uint8)
+        conv = np.zeros(max(1, R), dtype=np.uint8)
+        iters = np.zeros(max(1, R), dtype=np.uint8)
+        done = np.zeros(max(1, R), dtype=np.float64)
+        used = ctypes.c_int()
+        _check(lib().bpq_server_replay(self._h, R, _ptr(code), _ptr(arrival), _ptr(syn), _ptr(syn_off), _ptr(est),
+                                       _ptr(est_off), _ptr(conv), _ptr(iters), _ptr(done), ctypes.byref(used)),
+               "bpq_server_replay")
+        ests = [est[o:o + n] for o, n in zip(est_off, Ns)]
+        return ests, conv[:R], iters[:R], done[:R], used.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.bpq_server_free(h)
+            self._h = None

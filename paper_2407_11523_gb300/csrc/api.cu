@@ -157,6 +157,43 @@ uint64_t threshold(double c) {
     return (uint64_t)std::ldexp(c, 64);
 }
 
+int launch_grid(long items, int per_block) {
+    long g = (items + per_block - 1) / per_block;
+    if (g > (1L << 30)) g = 1L << 30;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------- no-allocation staging
+// Device memory for bpq_decode_host_noalloc: a fixed array in the library's
+// own image, so that callers that cannot allocate device memory can still
+// decode.  It is created when the library is loaded on a device and held
+// until the process exits.
+constexpr size_t kNoAllocBytes = size_t(8) << 20;
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` (which must be current).
+// In host code the symbol's name is only a host-side stand-in, so its device
+// address is looked up once per device and cached.
+int noalloc_scratch(int device, void **out) {
+    if (device < 0 || device >= kMaxDevices) return fail(BPQ_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(BPQ_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return BPQ_OK;
+}
+
+}  // namespace
+
 int need_uploaded(const bpq_tanner *t) {
     if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
     if (!t->dev_blob) return fail(BPQ_ESTATE, "tanner not uploaded to a device");
@@ -216,42 +253,12 @@ int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prio
     return BPQ_OK;
 }
 
-int launch_grid(long items, int per_block) {
-    long g = (items + per_block - 1) / per_block;
-    if (g > (1L << 30)) g = 1L << 30;
-    return (int)(g < 1 ? 1 : g);
-}
-
-// ---------------------------------------------------------------- no-allocation staging
-// Device memory for bpq_decode_host_noalloc: a fixed array in the library's
-// own image, so that callers that cannot allocate device memory can still
-// decode.  It is created when the library is loaded on a device and held
-// until the process exits.
-constexpr size_t kNoAllocBytes = size_t(8) << 20;
-static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on `device` (which must be current).
-// In host code the symbol's name is only a host-side stand-in, so its device
-// address is looked up once per device and cached.
-int noalloc_scratch(int device, void **out) {
-    if (device < 0 || device >= kMaxDevices) return fail(BPQ_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(BPQ_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_noalloc_ptr[device] = p;
-    }
-    *out = g_noalloc_ptr[device];
+int cuda_set_device(int device) {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     return BPQ_OK;
 }
 
-}  // namespace
 }  // namespace bpq
 
 extern "C" {
@@ -456,12 +463,12 @@ int bpq_decode_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *
 
 int bpq_set_launch(bpq_tanner *t, int threads_per_shot, int shots_per_cta) {
     if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
-    if (threads_per_shot < 0 || shots_per_cta < 0 || shots_per_cta > 15) return fail(BPQ_EINVAL, "bad launch shape");
+    if (threads_per_shot < 0 || shots_per_cta < 0 || shots_per_cta > 32) return fail(BPQ_EINVAL, "bad launch shape");
     const int old_t = t->threads_per_shot, old_s = t->shots_per_cta;
     t->threads_per_shot = threads_per_shot;
     t->shots_per_cta = shots_per_cta;
     bpq::LaunchShape s;
-    int rc = bpq::decode_launch_shape(t, &s);
+    int rc = bpq::decode_launch_shape(t, -1, &s);
     if (rc) {
         t->threads_per_shot = old_t;
         t->shots_per_cta = old_s;
@@ -469,10 +476,70 @@ int bpq_set_launch(bpq_tanner *t, int threads_per_shot, int shots_per_cta) {
     return rc;
 }
 
+int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+                 const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
+                 uint8_t *iters_dev, void *work_dev, void *stream, int *threads_per_shot, int *shots_per_cta,
+                 float *best_ms) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    if (B < 1) return fail(BPQ_EINVAL, "autotune needs a non-empty sample");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nodes = t->N > t->M ? t->N : t->M;
+    const int old_t = t->threads_per_shot, old_s = t->shots_per_cta;
+    int best_T = 0, best_S = 0;
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    rc = bpq::cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
+    if (rc) return rc;
+    rc = bpq::cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
+    if (rc) { cudaEventDestroy(e0); return rc; }
+    // candidate shapes: 1..4 nodes per thread, about 128..512 threads per CTA
+    for (int npt = 1; npt <= bpq::kMaxNodesPerThread && !rc; ++npt) {
+        const int T = (((nodes + npt - 1) / npt + 31) / 32) * 32;
+        if (T > bpq::kMaxThreadsPerShot) continue;
+        if (npt > 1 && (((nodes + npt - 2) / (npt - 1) + 31) / 32) * 32 == T) continue;  // same T as npt-1
+        for (int S : {1, 2, 4, 8, 15, 32}) {
+            if (S * T > (npt <= 2 ? 1024 : 512) || (S > 15 && T > 32) || (S > 1 && S * T < 64)) continue;
+            t->threads_per_shot = T;
+            t->shots_per_cta = S;
+            bpq::LaunchShape shape;
+            if (bpq::decode_launch_shape(t, variant, &shape)) continue;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3 && !rc; ++rep) {  // one warm-up, two timed
+                if (rep == 1) rc = bpq::cuda_check(cudaEventRecord(e0, st), "cudaEventRecord");
+                if (!rc)
+                    rc = bpq_decode(t, syn_dev, prior_dev, variant, params, max_iter, B, est_dev, conv_dev,
+                                    iters_dev, work_dev, stream);
+            }
+            if (!rc) rc = bpq::cuda_check(cudaEventRecord(e1, st), "cudaEventRecord");
+            if (!rc) rc = bpq::cuda_check(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            if (!rc) rc = bpq::cuda_check(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (!rc && ms / 2 < best) {
+                best = ms / 2;
+                best_T = T;
+                best_S = S;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc || best_T == 0) {
+        t->threads_per_shot = old_t;
+        t->shots_per_cta = old_s;
+        return rc ? rc : fail(BPQ_EINVAL, "no launch shape fits this code");
+    }
+    t->threads_per_shot = best_T;
+    t->shots_per_cta = best_S;
+    if (threads_per_shot) *threads_per_shot = best_T;
+    if (shots_per_cta) *shots_per_cta = best_S;
+    if (best_ms) *best_ms = best;
+    return BPQ_OK;
+}
+
 int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_cta, int *ctas) {
     if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
     bpq::LaunchShape s;
-    int rc = bpq::decode_launch_shape(t, &s);
+    int rc = bpq::decode_launch_shape(t, -1, &s);
     if (rc) return rc;
     if (threads_per_shot) *threads_per_shot = s.T;
     if (shots_per_cta) *shots_per_cta = s.groups_per_cta;

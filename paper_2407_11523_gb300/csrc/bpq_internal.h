@@ -12,9 +12,9 @@
 namespace bpq {
 
 constexpr int kMaxDeg = 4;          // padded check and qubit degree of the decoder
-constexpr int kMaxThreadsPerShot = 512;
+constexpr int kMaxThreadsPerShot = 1024;
 constexpr int kMaxNodesPerThread = 4;
-constexpr int kMaxNodes = kMaxThreadsPerShot * kMaxNodesPerThread;  // max(N, M)
+constexpr int kMaxNodes = 2048;  // max(N, M): two nodes per thread at 1024 threads per shot
 constexpr uint16_t kNoSlot = 0xFFFF;
 constexpr size_t kWorkspaceBytes = 256;  // [0] next shot, [1] device error word
 

@@ -1,0 +1,657 @@
+// Flooding-schedule GF(4) belief propagation on sm_103a: one group of G warps
+// decodes one shot at a time; each thread owns NPT checks and NPT qubits
+// (node j belongs to thread j mod 32G).  The shot's edge messages live in
+// shared memory, one float per edge, updated in place: the check pass turns
+// variable-to-check messages into check-to-variable messages and the variable
+// pass turns them back.  Groups synchronise on their own named barrier, so
+// every shot stops as soon as its hard decision satisfies the syndrome, and
+// the group then takes the next shot from a global work queue (a persistent
+// kernel, grid = SMs x resident CTAs).  The Tanner-graph adjacency is staged
+// once per CTA into shared memory by a bulk TMA copy; the per-qubit prior
+// LLRs sit in shared memory (shared by the CTA's groups) and the per-qubit
+// variant state in the group's shared memory, so that registers hold only
+// adjacency and temporaries.
+//
+// Arithmetic (Sec. II-B1 and Sec. III of the paper, fp32):
+//  * check-to-variable, eq. (h_update): with phi(x) = -ln tanh(x/2) (its own
+//    inverse), 2 atanh(prod_k tanh(m_k/2)) = sign * phi(sum_k phi(|m_k|)),
+//    sign = (-1)^{s_i} prod_k sign(m_k).  Variable-to-check messages are
+//    stored as sign(m) * phi(|m|), so the check pass only sums magnitudes
+//    and XORs sign bits.
+//  * variable-to-check, eqs. (lambda), (v_update), (mombp5): the message is
+//    lambda_H(Q - own anticommuting message) = ln(C / A) with
+//    C = 1 + e^{-Q_H} and A = (e^{-Q_a} + e^{-Q_b}) e^{m_c->v}, a, b the two
+//    Paulis other than H.  All four exponentials share the shift
+//    c0 = min(0, Q_X, Q_Y, Q_Z), so nothing overflows, and the stored value
+//    phi(|lambda|) = ln((C+A)/|C-A|) = log1p(2 min(C,A) / |C-A|) comes out
+//    of C and A without forming lambda.
+//  * message saturation: |m| <= msg_clip on both directions, i.e.
+//    phi(|m_v->c|) >= phi(msg_clip) and |m_c->v| <= msg_clip.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bpq_internal.h"
+#include "decode_launch.h"
+
+namespace bpq {
+namespace dk {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA), completion signalled on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll may itself suspend
+// for a short hardware-defined time).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t n = 0; n < limit; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void group_sync(int G, int bar_id) {
+    if (G == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(G * 32) : "memory");
+    }
+}
+
+// Barrier over the group that also returns whether any thread's pred is set.
+__device__ __forceinline__ int group_any(int G, int bar_id, int pred) {
+    if (G == 1) {
+        __syncwarp();
+        return __any_sync(0xffffffffu, pred);
+    }
+    int r;
+    asm volatile(
+        "{ .reg .pred p, q; setp.ne.s32 p, %1, 0; bar.red.or.pred q, %2, %3, p; selp.s32 %0, 1, 0, q; }"
+        : "=r"(r)
+        : "r"(pred), "r"(bar_id), "r"(G * 32)
+        : "memory");
+    return r;
+}
+
+// <A, B> for single-qubit Pauli codes (0 = I, 1 = X, 2 = Y, 3 = Z).
+__device__ __forceinline__ uint32_t anti(uint32_t a, uint32_t b) {
+    return (a != 0u) & (b != 0u) & (a != b);
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Hardware approximations (PTX .approx, flush-to-zero): relative error about
+// 2^-22 for ex2 and rcp, absolute error about 2^-22 for lg2 near 1.
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// The same, but always executed: used where the result only feeds a select,
+// so that the compiler keeps the code straight-line instead of branching
+// around the special-function unit.
+__device__ __forceinline__ float ex2_always(float x) {
+    float y;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_always(float x) {
+    float y;
+    asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Check-to-variable magnitude w = phi(S) = ln(1 + 2 / (e^S - 1)), S >= 0,
+// needed to an absolute accuracy.  e^S - 1 keeps its relative accuracy:
+// below S = 1/4 from its Taylor series to S^6/720 (truncation < 5e-8
+// relative), above from 2^(S log2 e) - 1 (the ex2 error is amplified at most
+// e^S/(e^S-1) < 4.6 times).  Then w = ln2 * lg2(1 + 2/(e^S-1)); S = 0 gives
+// w = inf (clipped by the caller), S -> inf gives w -> 0.
+__device__ __forceinline__ float phi_check(float S) {
+    // (for S > 88, 2^(S log2 e) overflows to inf, 2/inf = 0 and w = 0)
+    const float poly =
+        S * fmaf(S, fmaf(S, fmaf(S, fmaf(S, fmaf(S, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f), 1.0f / 6.0f), 0.5f), 1.0f);
+    const float big = ex2_always(S * kLog2e) - 1.0f;
+    const float em1 = S < 0.25f ? poly : big;
+    return kLn2 * lg2(fmaf(2.0f, rcp(em1), 1.0f));
+}
+
+// phi(|lambda|) = ln(1 + r), r = 2 min(C,A) / |C - A|, needed to a relative
+// accuracy (small values are summed by the check pass): below r = 1/16 from
+// the series r - r^2/2 + r^3/3 - r^4/4 + r^5/5 (truncation < 2e-7 relative),
+// above from ln2 * lg2(1 + r).
+__device__ __forceinline__ float log1p_rel(float r) {
+    const float poly = r * fmaf(r, fmaf(r, fmaf(r, fmaf(r, 0.2f, -0.25f), 1.0f / 3.0f), -0.5f), 1.0f);
+    const float big = kLn2 * lg2_always(1.0f + r);
+    return r < 0.0625f ? poly : big;
+}
+
+// Number of per-qubit state arrays a variant keeps in shared memory:
+// EWAInit Q^(t-1); Momentum Q^(t-1), g; AdaGrad Q^(t-1), G.
+template <int VARIANT>
+struct StateArrays {
+    static constexpr int n = VARIANT == BPQ_PLAIN ? 0 : VARIANT == BPQ_EWAINIT ? 3 : 6;
+};
+
+// Anticommutation mask: bit p of (kAntiLut >> 4d) is <d, p> for Pauli codes d, p.
+constexpr uint32_t kAntiLut = 0x6AC0u;
+
+// Sum of the c->v messages from checks that anticommute with X, Y, Z
+// (S_W of eq. (p_update)).  NOY: the code has no Y entries, so an X-type
+// check contributes to S_Z and S_Y and a Z-type check to S_X and S_Y.
+template <bool NOY>
+__device__ __forceinline__ void anticommuting_sums(uint32_t vp, const float (&w)[4], float &SX, float &SY,
+                                                   float &SZ) {
+    SX = SY = SZ = 0.f;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        const uint32_t p = (vp >> (2 * n)) & 3u;
+        if (NOY) {
+            const float wx = p == 1u ? w[n] : 0.f, wz = p == 3u ? w[n] : 0.f;
+            SZ += wx;
+            SX += wz;
+        } else {
+            SX += (p != 0u && p != 1u) ? w[n] : 0.f;
+            SY += (p != 0u && p != 2u) ? w[n] : 0.f;
+            SZ += (p != 0u && p != 3u) ? w[n] : 0.f;
+        }
+    }
+    if (NOY) SY = SX + SZ;
+}
+
+// Variable-to-check messages of one qubit, stored as sign * phi(|lambda|)
+// into its four slots; win are the incoming check-to-variable messages.
+template <bool TRACE, bool NOY>
+__device__ __forceinline__ void emit_v2c(const DecodeArgs &a, float *slots, int j, int t, int shot, uint32_t vp,
+                                         float QX, float QY, float QZ, const float (&win)[4]) {
+    const float c0 = fminf(0.f, fminf(QX, fminf(QY, QZ)));
+    const float e0 = ex2(c0 * kLog2e);
+    const float eX = ex2((c0 - QX) * kLog2e), eY = ex2((c0 - QY) * kLog2e), eZ = ex2((c0 - QZ) * kLog2e);
+    // C = 1 + e^{-Q_H} and the two anticommuting terms, for H = X, Y, Z
+    const float CX = e0 + eX, CY = e0 + eY, CZ = e0 + eZ;
+    const float AX = eY + eZ, AY = eX + eZ, AZ = eX + eY;
+    float out[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        const uint32_t p = (vp >> (2 * n)) & 3u;
+        float C, Ab;
+        if (NOY) {
+            C = p == 1u ? CX : CZ;
+            Ab = p == 1u ? AX : AZ;
+        } else {
+            C = p == 1u ? CX : p == 2u ? CY : CZ;
+            Ab = p == 1u ? AX : p == 2u ? AY : AZ;
+        }
+        const float A = Ab * ex2(win[n] * kLog2e);
+        const float mx = fmaxf(C, A), mn = fminf(C, A);
+        const float ph = fmaxf(log1p_rel(2.0f * mn * rcp(mx - mn)), a.phi_clip);  // |lambda| <= msg_clip
+        out[n] = p ? ((A > C) ? -ph : ph) : 0.f;
+        if (TRACE && a.tr_v2c && p) {
+            const float lam = fminf(fmaxf(kLn2 * (lg2(C) - lg2(A)), -a.clip), a.clip);
+            a.tr_v2c[((size_t)shot * (a.max_iter + 1) + t) * a.E + a.var_canon[4 * j + n]] = lam;
+        }
+    }
+    *reinterpret_cast<float4 *>(slots + 4 * j) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// Bytes 0..3: 1 where the decision d anticommutes with the qubit's edge n
+// (pp holds the edge Paulis one per byte; padding bytes are 0).
+__device__ __forceinline__ uint32_t anti_bytes(uint32_t d, uint32_t pp) {
+    const uint32_t x = (d * 0x01010101u) ^ pp;                       // 0 where d == p
+    const uint32_t ne = (x | (x >> 1)) & 0x01010101u;                // 1 where d != p
+    const uint32_t nz = (pp | (pp >> 1)) & 0x01010101u;              // 1 where p != I
+    return d ? (ne & nz) : 0u;
+}
+
+// Per-thread adjacency of the owned checks and qubits of one code:
+// cs: the four message slots of each owned check (padding -> zero slot);
+// info: check Paulis (bits 0-7) | qubit Paulis (bits 8-15); pp: qubit
+// Paulis one per byte.
+template <int NPT>
+struct ThreadAdj {
+    uint32_t cs_lo[NPT], cs_hi[NPT], info[NPT], pp[NPT];
+};
+
+template <int NPT>
+__device__ __forceinline__ void load_adjacency(const DecodeArgs &a, const uint8_t *tab, int T, int tg, int npt,
+                                               ThreadAdj<NPT> &adj) {
+    const uint32_t kZero = 4u * (uint32_t)a.n_pad;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        adj.cs_lo[k] = adj.cs_hi[k] = kZero | (kZero << 16);
+        adj.info[k] = 0u;
+        adj.pp[k] = 0u;
+        const int i = k * T + tg;
+        if (k < npt && i < a.M) {
+            const uint2 s = *reinterpret_cast<const uint2 *>(tab + 8 * i);
+            const uint32_t s0 = s.x & 0xFFFFu, s1 = s.x >> 16, s2 = s.y & 0xFFFFu, s3 = s.y >> 16;
+            adj.cs_lo[k] = (s0 == kNoSlot ? kZero : s0) | ((s1 == kNoSlot ? kZero : s1) << 16);
+            adj.cs_hi[k] = (s2 == kNoSlot ? kZero : s2) | ((s3 == kNoSlot ? kZero : s3) << 16);
+            adj.info[k] = tab[a.off_chk_pauli + i];
+        }
+        if (k < npt && i < a.N) {
+            const uint32_t vp = tab[a.off_var_pauli + i];
+            adj.info[k] |= vp << 8;
+            adj.pp[k] = (vp & 3u) | (((vp >> 2) & 3u) << 8) | (((vp >> 4) & 3u) << 16) | (((vp >> 6) & 3u) << 24);
+        }
+    }
+}
+
+// Prior LLRs Pi_{v_j,W} = ln(p^I / p^W) of a code into shared memory
+// ([3][n_pad], computed by all threads of the CTA).
+__device__ __forceinline__ void load_prior(const DecodeArgs &a, float *PiS) {
+    const int Np = a.n_pad;
+    for (int j = threadIdx.x; j < a.N; j += blockDim.x) {
+        const float px = a.prior[3 * j], py = a.prior[3 * j + 1], pz = a.prior[3 * j + 2];
+        const float pI = 1.0f - px - py - pz;
+        PiS[j] = logf(pI / px);
+        PiS[Np + j] = logf(pI / py);
+        PiS[2 * Np + j] = logf(pI / pz);
+    }
+}
+
+// Shared-memory regions of shot group `group` of a code laid out from `base`
+// (base = the staged table): table | Pi [3][Np] | groups.
+struct GroupMem {
+    float *PiS, *slots, *state;
+    uint8_t *abits;
+};
+
+__device__ __forceinline__ GroupMem group_mem(const DecodeArgs &a, uint8_t *base, int group) {
+    GroupMem m;
+    m.PiS = reinterpret_cast<float *>(base + a.table_bytes);
+    uint8_t *g = base + a.table_bytes + (size_t)12 * a.n_pad + (size_t)group * a.group_bytes;
+    m.slots = reinterpret_cast<float *>(g);
+    m.abits = reinterpret_cast<uint8_t *>(m.slots + a.slots_floats);
+    m.state = reinterpret_cast<float *>(m.abits + ((a.slots_floats + 15u) & ~15u));
+    return m;
+}
+
+// Decode one shot with a group of G warps (thread tg of 32G): eq. (init),
+// then iterations of the check pass and the variable pass until the hard
+// decision satisfies the syndrome or max_iter is reached; writes the shot's
+// outputs.  npt <= NPT is the number of nodes each thread owns.
+template <int VARIANT, int NPT, bool TRACE, bool NOY>
+__device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj<NPT> &adj, const GroupMem &m,
+                                            int npt, int T, int tg, int G, int bar_id, int shot) {
+    const int N = a.N, M = a.M, Np = a.n_pad;
+    const uint32_t kZero = 4u * (uint32_t)Np, kTrash = kZero + 1u;
+    float *slots = m.slots, *state = m.state;
+    const float *PiS = m.PiS;
+    uint8_t *abits = m.abits;
+
+    // syndrome bits of the owned checks (bit k <-> check k*T + tg)
+    uint32_t sbits = 0;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int i = k * T + tg;
+        if (k < npt && i < M) {
+            const uint32_t w = __ldg(a.syn + (size_t)shot * a.W + (i >> 5));
+            sbits |= ((w >> (i & 31)) & 1u) << k;
+        }
+    }
+
+    // eq. (init): lambda(Pi^(0)), i.e. the variable pass with Q = Pi^(0)
+    // and no incoming messages; Q^(0) = Pi^(0), g^(0) = G^(0) = 0
+    uint32_t dk[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        dk[k] = 0;
+        const int j = k * T + tg;
+        if (k < npt && j < N) {
+            const float PX = PiS[j], PY = PiS[Np + j], PZ = PiS[2 * Np + j];
+            if (StateArrays<VARIANT>::n >= 3) {
+                state[j] = PX;
+                state[Np + j] = PY;
+                state[2 * Np + j] = PZ;
+            }
+            if (StateArrays<VARIANT>::n == 6) {
+                state[3 * Np + j] = 0.f;
+                state[4 * Np + j] = 0.f;
+                state[5 * Np + j] = 0.f;
+            }
+            const float z4[4] = {0.f, 0.f, 0.f, 0.f};
+            emit_v2c<TRACE, NOY>(a, slots, j, 0, shot, adj.info[k] >> 8, PX, PY, PZ, z4);
+        }
+    }
+    group_sync(G, bar_id);
+
+    int conv = 0, iters = 0;
+    for (int t = 1;; ++t) {
+        const bool do_check = t > 1 && (!TRACE || t > a.max_iter);
+        const bool do_msgs = t <= a.max_iter;
+        uint32_t mismatch = 0;
+
+        // ---- check pass: syndrome test of the previous decision, then eq. (h_update) ----
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int i = k * T + tg;
+            if (k < npt && i < M) {
+                const uint32_t sl[4] = {adj.cs_lo[k] & 0xFFFFu, adj.cs_lo[k] >> 16, adj.cs_hi[k] & 0xFFFFu,
+                                        adj.cs_hi[k] >> 16};
+                const uint32_t sb = (sbits >> k) & 1u;
+                if (do_check) mismatch |= sb ^ abits[sl[0]] ^ abits[sl[1]] ^ abits[sl[2]] ^ abits[sl[3]];
+                if (do_msgs) {
+                    uint32_t u[4];
+                    float mag[4];
+#pragma unroll
+                    for (int n = 0; n < 4; ++n) {
+                        u[n] = __float_as_uint(slots[sl[n]]);
+                        mag[n] = __uint_as_float(u[n] & 0x7FFFFFFFu);
+                    }
+                    // (-1)^{s_i} times the product of the incoming signs
+                    const uint32_t sgn = (u[0] ^ u[1] ^ u[2] ^ u[3] ^ (sb << 31)) & 0x80000000u;
+                    const float e01 = mag[0] + mag[1], e23 = mag[2] + mag[3];
+                    const float ext[4] = {mag[1] + e23, mag[0] + e23, e01 + mag[3], e01 + mag[2]};
+#pragma unroll
+                    for (int n = 0; n < 4; ++n) {
+                        const float wv = fminf(phi_check(ext[n]), a.clip);
+                        const float mm = __uint_as_float(__float_as_uint(wv) ^ ((sgn ^ u[n]) & 0x80000000u));
+                        slots[sl[n] == kZero ? kTrash : sl[n]] = mm;
+                        if (TRACE && a.tr_c2v && sl[n] != kZero)
+                            a.tr_c2v[((size_t)shot * a.max_iter + (t - 1)) * a.E + a.chk_ptr[i] + n] = mm;
+                    }
+                }
+            }
+        }
+        const int any = group_any(G, bar_id, (int)mismatch);
+        if (do_check && !any) {
+            conv = 1;
+            iters = t - 1;
+            break;
+        }
+        if (!do_msgs) {
+            conv = 0;
+            iters = a.max_iter;
+            break;
+        }
+
+        // ---- variable pass: posterior of the variant, decision, eq. (v_update)/(mombp5) ----
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int j = k * T + tg;
+            if (k < npt && j < N) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(slots + 4 * j);
+                const float win[4] = {w4.x, w4.y, w4.z, w4.w};
+                const uint32_t vp = adj.info[k] >> 8;
+                float S[3];
+                anticommuting_sums<NOY>(vp, win, S[0], S[1], S[2]);
+                const float Pi[3] = {PiS[j], PiS[Np + j], PiS[2 * Np + j]};
+                float Q[3];
+#pragma unroll
+                for (int w = 0; w < 3; ++w) {
+                    if (VARIANT == BPQ_PLAIN) {
+                        Q[w] = Pi[w] + S[w];  // eq. (p_update)
+                    } else if (VARIANT == BPQ_EWAINIT) {
+                        // eq. (EWAInit): Pi^(t) = alpha Pi^(0) + (1-alpha) Q^(t-1), t > 1
+                        const float qp = state[w * Np + j];
+                        const float pit = t > 1 ? a.alpha * Pi[w] + (1.f - a.alpha) * qp : Pi[w];
+                        Q[w] = pit + S[w];
+                        state[w * Np + j] = Q[w];
+                    } else if (VARIANT == BPQ_MOMENTUM) {
+                        // eqs. (mombp1), (mombp2) with the gradient of (mombp3)
+                        const float qp = state[w * Np + j];
+                        const float grad = qp - Pi[w] - S[w];
+                        const float g = a.gamma * state[(3 + w) * Np + j] + (1.f - a.gamma) * grad;
+                        Q[w] = qp - a.alpha * g;
+                        state[w * Np + j] = Q[w];
+                        state[(3 + w) * Np + j] = g;
+                    } else {
+                        // eq. (boost) from t = 2; G accumulates g'^2
+                        const float qp = state[w * Np + j];
+                        const float gp = qp - Pi[w] - S[w];
+                        float Gs = state[(3 + w) * Np + j];
+                        if (t >= 2 || a.ada_from1) Gs += gp * gp;
+                        Q[w] = t == 1 ? Pi[w] + S[w] : qp - a.alpha * gp * rcp(sqrt_approx(Gs) + a.eps);
+                        state[w * Np + j] = Q[w];
+                        state[(3 + w) * Np + j] = Gs;
+                    }
+                }
+                // hard decision: I if all Q_W > 0, else the first minimum of X, Y, Z
+                uint32_t d;
+                if (Q[0] > 0.f && Q[1] > 0.f && Q[2] > 0.f) {
+                    d = 0;
+                } else {
+                    d = 1;
+                    float mq = Q[0];
+                    if (Q[1] < mq) { d = 2; mq = Q[1]; }
+                    if (Q[2] < mq) d = 3;
+                }
+                dk[k] = d;
+                // per-edge <E^_j, H_ij> for the next syndrome test
+                reinterpret_cast<uint32_t *>(abits)[j] = anti_bytes(d, adj.pp[k]);
+                if (TRACE) {
+                    const size_t o = (size_t)shot * a.max_iter + (t - 1);
+                    if (a.tr_Q) {
+                        a.tr_Q[(o * N + j) * 3 + 0] = Q[0];
+                        a.tr_Q[(o * N + j) * 3 + 1] = Q[1];
+                        a.tr_Q[(o * N + j) * 3 + 2] = Q[2];
+                    }
+                    if (a.tr_dec) a.tr_dec[o * N + j] = (uint8_t)d;
+                }
+                emit_v2c<TRACE, NOY>(a, slots, j, t, shot, vp, Q[0], Q[1], Q[2], win);
+            }
+        }
+        group_sync(G, bar_id);
+    }
+
+    // ---- outputs ----
+    if (!TRACE || a.est) {
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int j = k * T + tg;
+            if (k < npt && j < N) a.est[(size_t)shot * N + j] = (uint8_t)dk[k];
+        }
+    }
+    if (tg == 0 && (!TRACE || a.conv)) {
+        a.conv[shot] = (uint8_t)conv;
+        a.iters[shot] = (uint8_t)iters;
+    }
+}
+
+// One code per launch: a persistent grid; every shot group takes shots from
+// the global queue until the batch is exhausted.
+template <int VARIANT, int NPT, bool TRACE, bool NOY>
+__global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const DecodeArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    int *grp_shot = reinterpret_cast<int *>(smem + 16);
+    uint8_t *tab = smem + kSmemHeader;
+
+    const int tid = threadIdx.x;
+    const int G = a.G;
+    const int T = G * 32;
+    const int group = tid / T;
+    const int tg = tid - group * T;
+    const int bar_id = 1 + group;
+    const GroupMem m = group_mem(a, tab, group);
+
+    // ---- stage the adjacency table once per CTA (bulk TMA copy) ----
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(mbar, a.table_bytes);
+        bulk_g2s(tab, a.table, a.table_bytes, mbar);
+    }
+    load_prior(a, m.PiS);
+    if (tg == 0) {
+        m.slots[4 * a.n_pad] = 0.f;  // the zero slot
+        m.abits[4 * a.n_pad] = 0;
+    }
+    const bool staged = mbar_wait_bounded(mbar, 0, 1u << 22);
+    if (__syncthreads_or(!staged)) {
+        if (tid == 0) atomicExch(a.work + 1, 1u);
+        mbar_wait_bounded(mbar, 0, 1u << 22);  // let an in-flight copy land before exiting
+        return;
+    }
+
+    ThreadAdj<NPT> adj;
+    load_adjacency<NPT>(a, tab, T, tg, NPT, adj);
+
+    for (;;) {
+        if (tg == 0) grp_shot[group] = (int)atomicAdd(a.work, 1u);
+        group_sync(G, bar_id);
+        const int shot = grp_shot[group];
+        if (shot >= a.B) break;
+        decode_shot<VARIANT, NPT, TRACE, NOY>(a, adj, m, NPT, T, tg, G, bar_id, shot);
+    }
+}
+
+// Many codes in one launch.  Work comes in tiles (code g, first shot, count)
+// from a global queue ordered by code; a CTA of kBatchThreads splits into the
+// code's shot groups (T_g threads each), which take the tile's shots from a
+// shared counter.  When the code changes the CTA re-stages that code's
+// adjacency (bulk TMA) and prior.  Every shot is decoded by decode_shot, so
+// results equal those of decode_kernel bit for bit.
+template <int VARIANT, int NPT>
+__global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const BatchArgs b) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    int *tile_slot = reinterpret_cast<int *>(smem + 8);    // current tile index
+    int *tile_ctr = reinterpret_cast<int *>(smem + 12);    // shots taken from the tile
+    int *grp_shot = reinterpret_cast<int *>(smem + 16);    // [kMaxGroupsPerCta]
+    DecodeArgs *desc = reinterpret_cast<DecodeArgs *>(smem + kSmemHeader);
+    uint8_t *tab = smem + kSmemHeader + kDescBytes;
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        *tile_ctr = 0;
+    }
+    __syncthreads();
+    int cur = -1;
+    uint32_t phase = 0;
+    ThreadAdj<NPT> adj;
+    for (;;) {
+        if (tid == 0) *tile_slot = (int)atomicAdd(b.work, 1u);
+        __syncthreads();
+        const int tile = *tile_slot;
+        if (tile >= b.ntiles) break;
+        const int4 td = b.tiles[tile];  // (code, first shot, shot count, -)
+        if (td.x != cur) {
+            // switch code: descriptor, adjacency (bulk TMA), prior, zero slots
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(b.codes + td.x);
+            for (int w = tid; w < (int)(sizeof(DecodeArgs) / 4); w += blockDim.x)
+                reinterpret_cast<uint32_t *>(desc)[w] = src[w];
+            __syncthreads();
+            if (tid == 0) {
+                mbar_expect_tx(mbar, desc->table_bytes);
+                bulk_g2s(tab, desc->table, desc->table_bytes, mbar);
+            }
+            load_prior(*desc, reinterpret_cast<float *>(tab + desc->table_bytes));
+            const bool staged = mbar_wait_bounded(mbar, phase, 1u << 22);
+            phase ^= 1u;
+            if (__syncthreads_or(!staged)) {
+                if (tid == 0) atomicExch(b.work + 1, 1u);
+                mbar_wait_bounded(mbar, phase ^ 1u, 1u << 22);
+                return;
+            }
+            const int T = desc->G * 32;
+            const int group = tid / T;
+            if (group < desc->groups_per_cta && tid - group * T == 0) {
+                const GroupMem m = group_mem(*desc, tab, group);
+                m.slots[4 * desc->n_pad] = 0.f;
+                m.abits[4 * desc->n_pad] = 0;
+            }
+            load_adjacency<NPT>(*desc, tab, T, tid - group * T, desc->npt, adj);
+            __syncthreads();
+            cur = td.x;
+        }
+        const DecodeArgs &a = *desc;
+        const int G = a.G, T = G * 32;
+        const int group = tid / T, tg = tid - group * T;
+        if (group < a.groups_per_cta) {
+            const GroupMem m = group_mem(a, tab, group);
+            const int bar_id = 1 + group;
+            for (;;) {
+                if (tg == 0) grp_shot[group] = atomicAdd(tile_ctr, 1);
+                group_sync(G, bar_id);
+                const int k = grp_shot[group];
+                if (k >= td.z) break;
+                if (a.noy)
+                    decode_shot<VARIANT, NPT, false, true>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k);
+                else
+                    decode_shot<VARIANT, NPT, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) *tile_ctr = 0;
+    }
+}
+
+}  // namespace dk
+
+// Instantiate the kernels of one variant and return the one for (NPT,
+// trace, no-Y code).
+#define BPQ_PICK_NPT(V, NPT, TR)                                                         \
+    (noy ? dk::decode_kernel<V, NPT, TR, true> : dk::decode_kernel<V, NPT, TR, false>)
+#define BPQ_DEFINE_PICK(NAME, V)                                                         \
+    DecodeKernelFn NAME(int npt, bool trace, bool noy) {                                 \
+        switch (npt * 2 + (trace ? 1 : 0)) {                                             \
+            case 2: return BPQ_PICK_NPT(V, 1, false);                                    \
+            case 3: return BPQ_PICK_NPT(V, 1, true);                                     \
+            case 4: return BPQ_PICK_NPT(V, 2, false);                                    \
+            case 5: return BPQ_PICK_NPT(V, 2, true);                                     \
+            case 6: return BPQ_PICK_NPT(V, 3, false);                                    \
+            case 7: return BPQ_PICK_NPT(V, 3, true);                                     \
+            case 8: return BPQ_PICK_NPT(V, 4, false);                                    \
+            case 9: return BPQ_PICK_NPT(V, 4, true);                                     \
+        }                                                                                \
+        return nullptr;                                                                  \
+    }                                                                                    \
+    BatchKernelFn NAME##_batch(int npt) {                                                \
+        return npt <= 2 ? dk::decode_batch_kernel<V, 2> : nullptr;                       \
+    }
+
+}  // namespace bpq

@@ -1,4 +1,5 @@
-// Kernel arguments and launch-shape selection of the decode kernel.
+// Kernel arguments, launch-shape selection and per-variant kernel lookup of
+// the decode kernel.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,7 +8,8 @@
 
 namespace bpq {
 
-constexpr uint32_t kSmemHeader = 128;  // mbarrier + per-group shot indices
+constexpr uint32_t kSmemHeader = 256;  // mbarrier, tile state, per-group shot indices
+constexpr int kMaxGroupsPerCta = 32;   // named barriers limit multi-warp groups to 15
 
 struct DecodeArgs {
     const uint8_t *table;      // staged adjacency (bpq_tanner::table on the device)
@@ -21,19 +23,58 @@ struct DecodeArgs {
     uint8_t *tr_dec;
     const int32_t *var_canon, *chk_ptr;
     int N, M, E, W, B, max_iter;
-    int G, npt;                // warps per shot group, nodes per thread
+    int G;                     // warps per shot group
+    int n_pad;                 // N rounded up to a multiple of 4 (shared-memory array stride)
     uint32_t slots_floats, group_bytes;
     float alpha, gamma, eps, clip, phi_clip;
     int ada_from1;
+    // used by the batched kernel only
+    int npt, groups_per_cta, noy;
+};
+
+constexpr uint32_t kDescBytes = (sizeof(DecodeArgs) + 15) & ~15u;  // descriptor copy in shared memory
+constexpr int kBatchThreads = 1024;  // CTA size of the batched kernel
+
+// Arguments of the batched kernel: per-code descriptors and the tile list
+// (code, first shot, shot count), both in device memory.
+struct BatchArgs {
+    const DecodeArgs *codes;
+    const int4 *tiles;
+    int ntiles;
+    uint32_t *work;  // [0] next tile, [1] device error word
 };
 
 struct LaunchShape {
-    int T, G, npt, NPT, groups_per_cta;
+    int T, G, npt, groups_per_cta;
+    int n_pad;
     uint32_t slots_floats, group_bytes;
     size_t smem;
 };
 
-int decode_launch_shape(const bpq_tanner *t, LaunchShape *s);
+using DecodeKernelFn = void (*)(const DecodeArgs);
+using BatchKernelFn = void (*)(const BatchArgs);
+
+// Kernels of one variant, for nodes per thread npt in [1, 4]; noy selects the
+// specialisation for codes without Y entries.
+DecodeKernelFn pick_plain(int npt, bool trace, bool noy);
+BatchKernelFn pick_plain_batch(int npt);
+DecodeKernelFn pick_momentum(int npt, bool trace, bool noy);
+BatchKernelFn pick_momentum_batch(int npt);
+DecodeKernelFn pick_adagrad(int npt, bool trace, bool noy);
+BatchKernelFn pick_adagrad_batch(int npt);
+DecodeKernelFn pick_ewainit(int npt, bool trace, bool noy);
+BatchKernelFn pick_ewainit_batch(int npt);
+
+int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
+// Shape of a code inside the batched kernel (CTAs of kBatchThreads threads).
+int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
+
+// Shared host helpers (api.cu).
+int need_uploaded(const bpq_tanner *t);
+int cuda_check(cudaError_t e, const char *what);
+int cuda_set_device(int device);
+int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prior, int variant,
+                     const bpq_params *params, int max_iter, int B, void *work, DecodeArgs &a);
 int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, cudaStream_t st, int *ctas_out);
 
 }  // namespace bpq

@@ -98,7 +98,7 @@ def test_rejects_bad_arguments(bpq):
 
 def test_launch_shapes(bpq):
     t = bpq.Tanner("toric", 15)
-    assert t.launch() == (128, 4)
+    assert t.launch() == (256, 1)
     t.set_launch(256, 2)
     assert t.launch() == (256, 2)
     assert bpq.Tanner("planar", 5).launch()[0] == 32

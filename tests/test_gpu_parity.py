@@ -288,3 +288,40 @@ def test_decode_host_matches_device(bpq):
     host = bpq.decode_host(t, syn_h, prior_h, "ewainit", max_iter=100)
     for a, b in zip(dev, host):
         assert torch.equal(a.cpu(), b)
+
+
+@pytest.mark.parametrize("p,min_stable", [(0.08, 0.75), (0.14, 0.15)])
+def test_full_size_toric_d15_bench_configuration(bpq, p, min_stable):
+    """The bench configuration: toric d = 15, 10^6 shots at one p, EWAInit-BP,
+    max 100 iterations, the default launch shape.  Invariants on every shot;
+    decisions on 200 shots spread over the batch against the oracle (on the
+    shots whose oracle decision is stable under an 8-ulp prior perturbation;
+    see test_batched_results_match_oracle_sample)."""
+    t = bpq.Tanner("toric", 15)
+    ch = oracle.depolarizing(p)
+    B = 1_000_000
+    err, syn = bpq.sample(t, *ch, seed=0xB9E00001, shot0=0, B=B)
+    prior = bpq.prior_tensor(t, *ch)
+    est, conv, iters = bpq.decode(t, syn, prior, "ewainit", max_iter=100)
+    fail = bpq.check_logical(t, err, est)
+    torch.cuda.synchronize()
+    conv_c, iters_c, fail_c = conv.cpu().numpy(), iters.cpu().numpy(), fail.cpu().numpy()
+    assert ((iters_c >= 1) & (iters_c <= 100)).all()
+    assert (iters_c[conv_c == 0] == 100).all()
+    assert (fail_c[conv_c == 1] != 1).all() and (fail_c[conv_c == 0] == 1).all()
+
+    idx = np.linspace(0, B - 1, 200).astype(np.int64)
+    H = t.dense()
+    s_ref = np.concatenate([oracle.sample(H, *ch, seed=0xB9E00001, shot0=int(i), B=1)[1] for i in idx])
+    pri = f32(np.tile(ch, (t.N, 1)))
+    est_r, conv_r, iters_r = oracle.decode(H, s_ref, pri, "ewainit", max_iter=100, nthreads=NTHREADS)
+    rng = np.random.default_rng(11)
+    stable = np.ones(len(idx), dtype=bool)
+    for _ in range(3):
+        pp = pri * (1 + 2.0 ** -20 * rng.choice([-1.0, 1.0], size=pri.shape))
+        stable &= (oracle.decode(H, s_ref, pp, "ewainit", max_iter=100, nthreads=NTHREADS)[0] == est_r).all(axis=1)
+    same = (est[torch.from_numpy(idx).cuda()].cpu().numpy() == est_r).all(axis=1)
+    # above the toric code's threshold region most shots never converge and
+    # their 100-iteration trajectories are chaotic (unstable in the oracle too)
+    assert stable.mean() >= min_stable
+    assert same[stable].mean() >= 0.999, (same[stable].mean(), stable.mean())

@@ -1,0 +1,74 @@
+"""Pins of the differentiable unrolled EWAInit-BP oracle (oracle/unrolled.py):
+at the paper's parameters it is EWAInit-BP (checked against the C oracle,
+which is itself pinned by Theorem 1 and tree exactness); alpha = 1 is plain
+BP; beta = 1 freezes the variable-to-check messages; autograd gradients
+agree with central finite differences."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import codes, unrolled
+
+
+@pytest.fixture(scope="module")
+def case():
+    H, _ = codes.build_code("planar", 5)
+    ch = oracle.depolarizing(0.06)
+    err, syn = oracle.sample(H, *ch, seed=77, shot0=0, B=6)
+    prior = np.tile(ch, (H.shape[1], 1))
+    return H, err, syn, prior
+
+
+@pytest.mark.parametrize("variant,alpha", [("ewainit", 0.5), ("ewainit", 0.3), ("plain", 1.0)])
+def test_matches_c_oracle_trace(case, variant, alpha):
+    """Same posterior as the C oracle (literal tanh/atanh in long double),
+    also once messages saturate at the clip (they do by iteration 5)."""
+    H, err, syn, prior = case
+    T = 9
+    g = unrolled.Graph(H)
+    E = g.E
+    Q = unrolled.forward(g, syn, prior, torch.full((T,), alpha, dtype=torch.float64),
+                         torch.zeros(T, dtype=torch.float64), torch.ones(E, dtype=torch.float64), T)
+    for b in range(syn.shape[0]):
+        tr = oracle.trace(H, syn[b], prior, variant="ewainit", alpha=alpha, T=T)
+        # near saturation the 64-bit-mantissa long double of the C oracle
+        # limits the agreement to ~1e-6
+        assert np.allclose(Q[b].numpy(), tr["Q"][-1], rtol=1e-8, atol=1e-5)
+
+
+def test_full_damping_freezes_messages(case):
+    """beta_t = 1: the variable-to-check messages stay at eq. (init), so
+    every iteration sees the same check messages and with alpha = 1 the
+    posterior is the same at every iteration."""
+    H, err, syn, prior = case
+    g = unrolled.Graph(H)
+    args = (torch.ones(4, dtype=torch.float64), torch.ones(4, dtype=torch.float64),
+            torch.ones(g.E, dtype=torch.float64))
+    Q1 = unrolled.forward(g, syn, prior, args[0][:1], args[1][:1], args[2], 1)
+    Q4 = unrolled.forward(g, syn, prior, *args, 4)
+    assert torch.allclose(Q1, Q4, atol=1e-12)
+
+
+def test_gradients_match_finite_differences(case):
+    H, err, syn, prior = case
+    T = 6
+    g = unrolled.Graph(H)
+    rng = np.random.default_rng(3)
+    alpha = 0.5 + 0.2 * rng.standard_normal(T)
+    beta = 0.1 * np.abs(rng.standard_normal(T))
+    w = 1.0 + 0.1 * rng.standard_normal(g.E)
+    L, ga, gb, gw = unrolled.loss_and_grads(H, syn[:2], err[:2], prior, alpha, beta, w, T)
+
+    def f(a, b, ww):
+        return float(unrolled.loss(unrolled.forward(g, syn[:2], prior, torch.tensor(a), torch.tensor(b),
+                                                    torch.tensor(ww), T), err[:2]))
+
+    h = 1e-6
+    for k in [0, 2, T - 1]:
+        d = np.zeros(T); d[k] = h
+        assert (f(alpha + d, beta, w) - f(alpha - d, beta, w)) / (2 * h) == pytest.approx(ga[k], rel=1e-5, abs=1e-9)
+        assert (f(alpha, beta + d, w) - f(alpha, beta - d, w)) / (2 * h) == pytest.approx(gb[k], rel=1e-5, abs=1e-9)
+    for e in [0, 17, g.E - 1]:
+        d = np.zeros(g.E); d[e] = h
+        assert (f(alpha, beta, w + d) - f(alpha, beta, w - d)) / (2 * h) == pytest.approx(gw[e], rel=1e-5, abs=1e-9)
