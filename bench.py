@@ -53,9 +53,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
-    ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve"],
+    ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve", "train"],
                     help="toric15: the headline sweep; mixed: many codes in one batched launch; "
-                         "serve: continuous-batching server on a Poisson request stream")
+                         "serve: continuous-batching server on a Poisson request stream; "
+                         "train: differentiable unrolled EWAInit-BP (forward + backward kernels)")
     ap.add_argument("--loads", default="1e4,1e5,1e6,1e7", help="offered loads (requests/s) for --workload serve")
     return ap.parse_args()
 
@@ -329,7 +330,21 @@ def run_ours(args, rank, world):
         lat[f"batch_{nb}"] = {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
                               "launches": len(times)}
 
-    # roofline of the decode kernel: SFU-bound in-SM arithmetic
+    # roofline of the decode kernel: SFU-bound in-SM arithmetic.  DRAM traffic
+    # per shot comes from the committed ncu summary, used only while the
+    # kernel source still matches the profiled one.
+    traffic = None
+    try:
+        import hashlib
+        prof = open(os.path.join(ROOT, "profiles", "decode_kernel_toric15_ewainit.md")).read()
+        src = open(os.path.join(ROOT, "paper_2407_11523_gb300", "csrc", "decode_kernel.cuh"), "rb").read()
+        want = [ln.split(":")[1].strip() for ln in prof.splitlines() if ln.startswith("kernel_source_sha256_16:")][0]
+        per_shot = float([ln for ln in prof.splitlines() if "traffic_bytes_per_shot:" in ln][0]
+                         .split("traffic_bytes_per_shot:")[1].split()[0])
+        if hashlib.sha256(src).hexdigest()[:16] == want:
+            traffic = per_shot * args.shots_per_p
+    except (OSError, IndexError, ValueError):
+        traffic = None
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sfu_peak = float("nan") if args.no_probe else bpq.probe_peak("sfu", blocks=sms * 8, threads=256, iters=4096)
     fma_peak = float("nan") if args.no_probe else bpq.probe_peak("fma", blocks=sms * 8, threads=256, iters=4096)
@@ -338,7 +353,7 @@ def run_ours(args, rank, world):
     kernel_sec = ew["launch_ms_mean"] / 1e3
     achieved = sfu_per_edge_update * (ew["edge_updates_per_step"] / len(P_SWEEP)) / kernel_sec
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": sfu_peak / 1e12, "unit": "TSFUop/s",
-                "frac": achieved / sfu_peak, "traffic": None,
+                "frac": achieved / sfu_peak, "traffic": traffic,
                 "kernel": "decode_kernel<EWAINIT>", "per_unit": f"{sfu_per_edge_update} SFU ops per edge-update",
                 "peak_source": "measured on this GPU by the MUFU.EX2 probe kernel (bpq_probe_peak)",
                 "fma_peak_tinst_per_s": fma_peak / 1e12, "sms": sms,
@@ -562,6 +577,94 @@ def run_serve(args, rank, world):
                 "gpu_launches": None}
         print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------ training workload
+
+def run_train(args, rank, world):
+    import torch
+
+    import paper_2407_11523_gb300 as bpq
+
+    T, K, B, d = 25, 5, 4096, 9
+    t = bpq.Tanner("planar", d).upload()
+    ps = np.linspace(0.03, 0.10, 8)
+    p0 = float(ps.mean())
+    prior = bpq.prior_tensor(t, p0 / 3, p0 / 3, p0 / 3)
+
+    def draw(seed, shot0, n_per_p):
+        errs, syns = [], []
+        for k, p in enumerate(ps):
+            e, s_ = bpq.sample(t, p / 3, p / 3, p / 3, seed=seed + k, shot0=shot0, B=n_per_p)
+            errs.append(e)
+            syns.append(s_)
+        return torch.cat(errs), torch.cat(syns)
+
+    # a fresh batch every step (Philox shot offsets advance), drawn before timing
+    n_batches = args.warmup + args.steps + 100
+    pool = [draw(SEED + 3000, (rank * n_batches + k) * (B // len(ps)), B // len(ps)) for k in range(n_batches)]
+    a = torch.full((T,), 0.5, device="cuda", requires_grad=True)
+    b = torch.zeros(T, device="cuda", requires_grad=True)
+    w = torch.ones(t.E, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([a, b, w], lr=0.01)
+    it = iter(pool)
+
+    def step():
+        err, syn = next(it)
+        opt.zero_grad()
+        L = bpq.unrolled_loss(t, syn, err, prior, a, b, w, T=T, ckpt_every=K)
+        L.backward()
+        opt.step()
+        with torch.no_grad():
+            a.clamp_(0.0, 1.0)
+            b.clamp_(0.0, 0.95)
+        return L.detach()
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        L = step()
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / args.steps
+    losses = [float(step()) for _ in range(100)]  # keep training for the accuracy comparison (not timed)
+
+    # held-out logical error rates: trained vs untrained unrolled decoder vs the early-exit kernel
+    err_t, syn_t = draw(SEED + 4000, 10**7 + rank * 65536, 8192)
+
+    def ler_from_Q(Q):
+        # hard decision of Sec. II-B1 on the final posterior (evaluation only)
+        allpos = (Q > 0).all(-1)
+        est = torch.where(allpos, torch.zeros_like(allpos, dtype=torch.long), 1 + Q.argmin(-1))
+        fail = bpq.check_logical(t, err_t, est.to(torch.uint8).contiguous())
+        return float((fail > 0).float().mean())
+
+    with torch.no_grad():
+        Qtr, Ltr = bpq.unrolled_posterior(t, syn_t, err_t, prior, a, b, w, T=T)
+        Q0, L0 = bpq.unrolled_posterior(t, syn_t, err_t, prior, torch.full_like(a, 0.5), torch.zeros_like(b),
+                                        torch.ones_like(w), T=T)
+    est_k, conv_k, _ = bpq.decode(t, syn_t, prior, "ewainit", max_iter=T, alpha=0.5)
+    ler_kernel = float((bpq.check_logical(t, err_t, est_k) > 0).float().mean())
+    if rank == 0:
+        line = {"metric": "differentiable unrolled EWAInit-BP: training shots/s (forward + hand-written backward)",
+                "value": B / sec, "unit": "shots/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"planar d={d} (N={t.N}, E={t.E}), T={T}, checkpoints every {K}, batch {B} "
+                                       f"depolarising errors at p in {[round(float(x), 3) for x in ps]}, "
+                                       f"prior p={p0:.3f}; "
+                                       "trainable alpha_t, beta_t (T each) and w_e (E); Adam lr 0.01, a fresh "
+                                       "Philox batch every step, 108 steps"},
+                "train_loss_first_last": [losses[0], losses[-1]],
+                "held_out_loss": {"trained": float(Ltr), "untrained": float(L0)},
+                "held_out_ler": {"trained_unrolled": ler_from_Q(Qtr), "untrained_unrolled": ler_from_Q(Q0),
+                                 "ewainit_kernel_early_exit": ler_kernel, "shots": int(err_t.shape[0])},
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
@@ -571,6 +674,8 @@ def main():
         run_mixed(args, rank, world)
     elif args.workload == "serve":
         run_serve(args, rank, world)
+    elif args.workload == "train":
+        run_train(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

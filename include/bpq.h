@@ -298,6 +298,33 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
 
 void bpq_server_free(bpq_server *s);
 
+/* ---------------------------------------------------------------- differentiable decoding */
+
+/* Unrolled EWAInit-BP with trainable parameters (an extension in the
+ * direction of neural BP named in the paper's conclusion): T flooding
+ * iterations of Algorithm 2 without the stopping rule, where iteration t
+ * uses its own EWA weight alpha_t (eq. (EWAInit)), damps the
+ * variable-to-check messages as (1 - beta_t) lambda(...) + beta_t m^(t-1),
+ * and scales each check-to-variable message by a weight w_e (E weights in
+ * the check-major edge order of bpq_tanner_export).  alpha_t = alpha,
+ * beta_t = 0, w_e = 1 is EWAInit-BP.  Loss: the mean over shots and qubits
+ * of -log softmax(0, -Q_X, -Q_Y, -Q_Z)[true Pauli] of the final posterior.
+ * Inputs: syn_dev [B][ceil(M/32)], err_dev [B][N] Pauli codes (the true
+ * errors), prior_dev [N][3]; alpha_dev, beta_dev [T], w_dev [E] (device
+ * float).  Codes of up to 1024 nodes; T <= 255.  The forward pass stores a
+ * checkpoint every ckpt_every iterations in work_dev; bpq_train_backward
+ * (same inputs, after the forward on the same workspace) recomputes each
+ * segment from its checkpoint and writes d loss / d alpha, beta, w.
+ * Results are deterministic.  Q_dev (optional) receives Q^(T) [B][N][3]. */
+size_t bpq_train_workspace_bytes(const bpq_tanner *t, int B, int T, int ckpt_every);
+int bpq_train_forward(const bpq_tanner *t, const uint32_t *syn_dev, const uint8_t *err_dev, const float *prior_dev,
+                      int B, int T, int ckpt_every, const float *alpha_dev, const float *beta_dev, const float *w_dev,
+                      float msg_clip, float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes, void *stream);
+int bpq_train_backward(const bpq_tanner *t, const uint32_t *syn_dev, const uint8_t *err_dev, const float *prior_dev,
+                       int B, int T, int ckpt_every, const float *alpha_dev, const float *beta_dev, const float *w_dev,
+                       float msg_clip, float *grad_alpha_dev, float *grad_beta_dev, float *grad_w_dev, void *work_dev,
+                       size_t work_bytes, void *stream);
+
 /* ---------------------------------------------------------------- evaluation */
 
 /* Success criterion of Sec. IV: E^ in E S.  For each shot the residual

@@ -79,6 +79,9 @@ def lib():
             "bpq_server_create": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, i, P, sz, PP]),
             "bpq_server_replay": (i, [P, i, P, P, P, P, P, P, P, P, P, pi]),
             "bpq_server_free": (None, [P]),
+            "bpq_train_workspace_bytes": (sz, [P, i, i, i]),
+            "bpq_train_forward": (i, [P, P, P, P, i, i, i, P, P, P, ctypes.c_float, P, P, P, sz, P]),
+            "bpq_train_backward": (i, [P, P, P, P, i, i, i, P, P, P, ctypes.c_float, P, P, P, P, sz, P]),
             "bpq_last_error": (ctypes.c_char_p, []),
             "bpq_version": (i, []),
         }
@@ -451,3 +454,55 @@ class Server:
         if h is not None and h.value and _lib is not None:
             _lib.bpq_server_free(h)
             self._h = None
+
+
+class _UnrolledEWAInit(torch.autograd.Function):
+    """Loss of the unrolled EWAInit-BP decoder as a function of its
+    parameters (alpha, beta, w); forward and backward run in libbpq's CUDA
+    kernels (bpq_train_forward / bpq_train_backward)."""
+
+    @staticmethod
+    def forward(ctx, alpha, beta, w, tanner, syn, err, prior, T, ckpt_every, msg_clip):
+        alpha, beta, w = alpha.contiguous().float(), beta.contiguous().float(), w.contiguous().float()
+        B = syn.shape[0]
+        nbytes = lib().bpq_train_workspace_bytes(tanner.handle, B, T, ckpt_every)
+        work = torch.empty(nbytes, dtype=torch.uint8, device=syn.device)
+        loss = torch.empty(1, dtype=torch.float32, device=syn.device)
+        _check(lib().bpq_train_forward(tanner.handle, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every,
+                                       _ptr(alpha), _ptr(beta), _ptr(w), msg_clip, _ptr(loss), None, _ptr(work),
+                                       nbytes, _stream(None)), "bpq_train_forward")
+        ctx.save_for_backward(alpha, beta, w)
+        ctx.rest = (tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gout):
+        alpha, beta, w = ctx.saved_tensors
+        tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes = ctx.rest
+        ga, gb, gw = torch.empty_like(alpha), torch.empty_like(beta), torch.empty_like(w)
+        _check(lib().bpq_train_backward(tanner.handle, _ptr(syn), _ptr(err), _ptr(prior), syn.shape[0], T,
+                                        ckpt_every, _ptr(alpha), _ptr(beta), _ptr(w), msg_clip, _ptr(ga), _ptr(gb),
+                                        _ptr(gw), _ptr(work), nbytes, _stream(None)), "bpq_train_backward")
+        return ga * gout, gb * gout, gw * gout, None, None, None, None, None, None, None
+
+
+def unrolled_loss(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0):
+    """Differentiable loss of the unrolled EWAInit-BP decoder (see
+    bpq_train_forward); gradients flow to alpha (T,), beta (T,) and w (E,)."""
+    tanner.upload()
+    return _UnrolledEWAInit.apply(alpha, beta, w, tanner, syn, err, prior, T, ckpt_every, msg_clip)
+
+
+def unrolled_posterior(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0):
+    """Final posterior Q^(T) (B, N, 3) and the loss of the unrolled decoder."""
+    tanner.upload()
+    B = syn.shape[0]
+    nbytes = lib().bpq_train_workspace_bytes(tanner.handle, B, T, ckpt_every)
+    work = torch.empty(nbytes, dtype=torch.uint8, device=syn.device)
+    loss = torch.empty(1, dtype=torch.float32, device=syn.device)
+    Q = torch.empty((B, tanner.N, 3), dtype=torch.float32, device=syn.device)
+    a, b, ww = alpha.contiguous().float(), beta.contiguous().float(), w.contiguous().float()
+    _check(lib().bpq_train_forward(tanner.handle, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every, _ptr(a),
+                                   _ptr(b), _ptr(ww), msg_clip, _ptr(loss), _ptr(Q), _ptr(work), nbytes,
+                                   _stream(None)), "bpq_train_forward")
+    return Q, loss[0]

@@ -1,0 +1,126 @@
+"""Differentiable unrolled EWAInit-BP on the GPU (bpq_train_forward /
+bpq_train_backward behind a torch.autograd.Function) against the float64
+oracle (oracle/unrolled.py): the loss, the gradients of the oracle
+(autograd) and FP64 central finite differences of the oracle forward."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import unrolled
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bpq():
+    import paper_2407_11523_gb300 as bpq
+    return bpq
+
+
+def setup(bpq, B, p, seed, d=9):
+    t = bpq.Tanner("planar", d)
+    ch = oracle.depolarizing(p)
+    err, syn = bpq.sample(t, *ch, seed=seed, shot0=0, B=B)
+    prior = bpq.prior_tensor(t, *ch)
+    return t, err, syn, prior, ch
+
+
+def params(T, E, seed, spread=0.0):
+    rng = np.random.default_rng(seed)
+    a = 0.5 + spread * rng.standard_normal(T)
+    b = spread * np.abs(rng.standard_normal(T))
+    w = 1.0 + spread * rng.standard_normal(E)
+    return a, b, w
+
+
+def oracle_inputs(t, err, syn, ch):
+    from inputs import unpack_bits
+    H = t.dense()
+    s = unpack_bits(syn.cpu().numpy().view(np.uint32), t.M)
+    e = err.cpu().numpy()
+    prior = np.tile(np.asarray(ch, dtype=np.float32).astype(np.float64), (t.N, 1))
+    return H, s, e, prior
+
+
+@pytest.mark.parametrize("T,K", [(8, 5), (25, 5), (25, 25)])
+def test_loss_matches_oracle(bpq, T, K):
+    t, err, syn, prior, ch = setup(bpq, 32, 0.05, 1)
+    a, b, w = params(T, t.E, 2, spread=0.05)
+    L = bpq.unrolled_loss(t, syn, err, prior, torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda"),
+                          torch.tensor(w, device="cuda"), T=T, ckpt_every=K)
+    H, s, e, pri = oracle_inputs(t, err, syn, ch)
+    Lr = float(unrolled.loss(unrolled.forward(unrolled.Graph(H), s, pri, torch.tensor(a), torch.tensor(b),
+                                              torch.tensor(w), T), e))
+    assert float(L) == pytest.approx(Lr, rel=2e-4)
+
+
+@pytest.mark.parametrize("T", [6, 12])
+def test_gradients_match_oracle_and_finite_differences(bpq, T):
+    t, err, syn, prior, ch = setup(bpq, 8, 0.06, 3)
+    a, b, w = params(T, t.E, 4, spread=0.1)
+    ta = torch.tensor(a, device="cuda", dtype=torch.float32, requires_grad=True)
+    tb = torch.tensor(b, device="cuda", dtype=torch.float32, requires_grad=True)
+    tw = torch.tensor(w, device="cuda", dtype=torch.float32, requires_grad=True)
+    L = bpq.unrolled_loss(t, syn, err, prior, ta, tb, tw, T=T, ckpt_every=5)
+    L.backward()
+    ga, gb, gw = (x.grad.detach().cpu().numpy().astype(np.float64) for x in (ta, tb, tw))
+    H, s, e, pri = oracle_inputs(t, err, syn, ch)
+    Lr, ra, rb, rw = unrolled.loss_and_grads(H, s, e, pri, a, b, w, T)
+    for g, r in ((ga, ra), (gb, rb), (gw, rw)):
+        scale = np.abs(r).max()
+        assert np.abs(g - r).max() <= 2e-3 * scale + 1e-7, (np.abs(g - r).max(), scale)
+    # FP64 central differences of the oracle forward, for a few coordinates
+    g = unrolled.Graph(H)
+
+    def f(aa, bb, ww):
+        return float(unrolled.loss(unrolled.forward(g, s, pri, torch.tensor(aa), torch.tensor(bb),
+                                                    torch.tensor(ww), T), e))
+
+    h = 1e-6
+    for k in (1, T - 1):
+        dv = np.zeros(T); dv[k] = h
+        fd = (f(a + dv, b, w) - f(a - dv, b, w)) / (2 * h)
+        assert ga[k] == pytest.approx(fd, rel=5e-3, abs=1e-6)
+    for k in (3, 100, t.E - 1):
+        dv = np.zeros(t.E); dv[k] = h
+        fd = (f(a, b, w + dv) - f(a, b, w - dv)) / (2 * h)
+        assert gw[k] == pytest.approx(fd, rel=5e-3, abs=1e-6)
+
+
+def test_backward_is_deterministic_and_checkpoint_independent(bpq):
+    t, err, syn, prior, ch = setup(bpq, 64, 0.07, 5)
+    T = 25
+    a, b, w = params(T, t.E, 6, spread=0.05)
+    grads = []
+    for K in (5, 5, 25, 7):
+        ta = torch.tensor(a, device="cuda", dtype=torch.float32, requires_grad=True)
+        tb = torch.tensor(b, device="cuda", dtype=torch.float32, requires_grad=True)
+        tw = torch.tensor(w, device="cuda", dtype=torch.float32, requires_grad=True)
+        bpq.unrolled_loss(t, syn, err, prior, ta, tb, tw, T=T, ckpt_every=K).backward()
+        grads.append([x.grad.clone() for x in (ta, tb, tw)])
+    for g0, g1 in zip(grads[0], grads[1]):
+        assert torch.equal(g0, g1)
+    for gk in grads[2:]:
+        for g0, g1 in zip(grads[0], gk):
+            assert torch.equal(g0, g1)  # recomputation reproduces the forward exactly
+
+
+def test_training_lowers_the_loss(bpq):
+    t, err, syn, prior, ch = setup(bpq, 1024, 0.06, 9)
+    T = 25
+    a = torch.full((T,), 0.5, device="cuda", requires_grad=True)
+    b = torch.zeros(T, device="cuda", requires_grad=True)
+    w = torch.ones(t.E, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([a, b, w], lr=0.02)
+    losses = []
+    for _ in range(15):
+        opt.zero_grad()
+        L = bpq.unrolled_loss(t, syn, err, prior, a, b, w, T=T)
+        L.backward()
+        opt.step()
+        with torch.no_grad():
+            a.clamp_(0.0, 1.0)
+            b.clamp_(0.0, 0.95)
+        losses.append(float(L))
+    assert losses[-1] < losses[0]
