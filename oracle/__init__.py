@@ -24,8 +24,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_oracle.so")
 _SOURCES = [os.path.join(_HERE, f) for f in ("bp_oracle.c", "noise_oracle.c")]
 
-PLAIN, MOMENTUM, ADAGRAD, EWAINIT = 0, 1, 2, 3
-VARIANTS = {"plain": PLAIN, "momentum": MOMENTUM, "adagrad": ADAGRAD, "ewainit": EWAINIT}
+PLAIN, MOMENTUM, ADAGRAD, EWAINIT, AEWA = 0, 1, 2, 3, 4
+VARIANTS = {"plain": PLAIN, "momentum": MOMENTUM, "adagrad": ADAGRAD, "ewainit": EWAINIT, "aewa": AEWA}
 
 # Parameters taken from the paper (Sec. III-A2, Sec. IV-A, Table I):
 # AdaGrad alpha = 5; Momentum gamma = 0 with alpha = 0.5; EWAInit alpha = 0.5.
@@ -34,6 +34,7 @@ DEFAULT_PARAMS = {
     MOMENTUM: dict(alpha=0.5, gamma=0.0),
     ADAGRAD: dict(alpha=5.0, gamma=0.0),
     EWAINIT: dict(alpha=0.5, gamma=0.0),
+    AEWA: dict(alpha=1.0, gamma=0.0),  # alpha is swept 1.0 .. 0.0 (Appendix C)
 }
 
 

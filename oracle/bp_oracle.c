@@ -27,6 +27,9 @@
  *                                                          g', G definitions below it
  *   EWAInit-BP         Pi^(t) = alpha Pi^(0) + (1-alpha)   Sec. III-B, Algorithm 2,
  *                      Q^(t-1)                             eq. (EWAInit)
+ *   AEWA-BP            EWAInit-BP with alpha = 1.0, 0.9,   Appendix C
+ *                      ..., 0.0 in turn until a run
+ *                      converges
  *
  * Readings taken where the paper is silent or ambiguous (each one is listed
  * in the design notes of the repository):
@@ -57,7 +60,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_PLAIN = 0, OR_MOMENTUM = 1, OR_ADAGRAD = 2, OR_EWAINIT = 3 };
+enum { OR_PLAIN = 0, OR_MOMENTUM = 1, OR_ADAGRAD = 2, OR_EWAINIT = 3, OR_AEWA = 4 };
 
 /* Trace-product <A, B>: 1 when the single-qubit Paulis anticommute. */
 static int anticommutes(int a, int b) { return a != 0 && b != 0 && a != b; }
@@ -345,14 +348,32 @@ typedef struct {
     int status;
 } job;
 
+/* AEWA-BP (Appendix C): EWAInit-BP with the discount factor taken from
+ * 1.0, 0.9, ..., 0.0 in turn (11 values, large to small) until a run
+ * converges; the outputs are those of the last run. */
+static int decode_shot_aewa(const graph *g, const uint8_t *syn, const double *prior, const params *pr,
+                            int max_iter, workspace *w, uint8_t *est_out, int *converged) {
+    int it = 0;
+    for (int k = 0; k <= 10; ++k) {
+        params p = *pr;
+        p.alpha = 1.0 - 0.1 * k;
+        it = decode_shot(g, syn, prior, OR_EWAINIT, &p, max_iter, 1, w, est_out, converged, NULL);
+        if (it < 0 || *converged) break;
+    }
+    return it;
+}
+
 static void *run_job(void *arg) {
     job *jb = arg;
     workspace w;
     if (ws_alloc(&w, jb->g->N, jb->g->E)) { jb->status = -1; ws_free(&w); return NULL; }
     for (int b = jb->b0; b < jb->b1; ++b) {
         int cv = 0;
-        int it = decode_shot(jb->g, jb->syn + (size_t)b * jb->g->M, jb->prior, jb->variant, jb->pr,
-                             jb->max_iter, 1, &w, jb->est + (size_t)b * jb->g->N, &cv, NULL);
+        int it = jb->variant == OR_AEWA
+                     ? decode_shot_aewa(jb->g, jb->syn + (size_t)b * jb->g->M, jb->prior, jb->pr, jb->max_iter, &w,
+                                        jb->est + (size_t)b * jb->g->N, &cv)
+                     : decode_shot(jb->g, jb->syn + (size_t)b * jb->g->M, jb->prior, jb->variant, jb->pr,
+                                   jb->max_iter, 1, &w, jb->est + (size_t)b * jb->g->N, &cv, NULL);
         if (it < 0) { jb->status = it; break; }
         jb->conv[b] = (uint8_t)cv;
         jb->iters[b] = it;
@@ -368,7 +389,7 @@ int oracle_decode(int N, int M, const uint8_t *H, int B, const uint8_t *syn, con
                   int variant, double alpha, double gamma, double eps, double msg_clip,
                   int adagrad_g_from_iter1, int max_iter, uint8_t *est, uint8_t *conv,
                   int32_t *iters, int nthreads) {
-    if (N <= 0 || M < 0 || B < 0 || max_iter < 1 || variant < 0 || variant > 3) return -1;
+    if (N <= 0 || M < 0 || B < 0 || max_iter < 1 || variant < 0 || variant > 4) return -1;
     graph g;
     if (graph_build(&g, N, M, H)) { graph_free(&g); return -2; }
     params pr = {alpha, gamma, eps, msg_clip, adagrad_g_from_iter1};

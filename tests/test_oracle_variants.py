@@ -120,3 +120,43 @@ def test_adagrad_small_rate_freezes_posterior(shots):
     H, syns, prior = shots
     tr = oracle.trace(H, syns[0], prior, variant="adagrad", alpha=1e-9, T=6)
     assert np.allclose(tr["Q"][1:], tr["Q"][0][None], atol=1e-7)
+
+
+@pytest.fixture(scope="module")
+def aewa_runs():
+    """Planar d = 7 at depolarising p = 0.08 (one of the Appendix C
+    workloads): AEWA-BP and EWAInit-BP at each of its eleven alphas."""
+    H, _ = codes.build_code("planar", 7)
+    ch = oracle.depolarizing(0.08)
+    _, syn = oracle.sample(H, *ch, seed=77, shot0=0, B=600)
+    prior = np.tile(ch, (H.shape[1], 1))
+    aewa = oracle.decode(H, syn, prior, variant="aewa", max_iter=60, nthreads=4)
+    runs = [oracle.decode(H, syn, prior, variant="ewainit", alpha=1.0 - 0.1 * k, max_iter=60, nthreads=4)
+            for k in range(11)]
+    plain = oracle.decode(H, syn, prior, variant="plain", max_iter=60, nthreads=4)
+    return aewa, runs, plain
+
+
+def test_aewa_takes_the_first_converging_alpha(aewa_runs):
+    """Appendix C: alpha = 1.0, 0.9, ..., 0.0 is tried in turn and the first
+    run that satisfies the syndrome is the output; if none does, the output is
+    the alpha = 0 run, unconverged.  Brute force over the eleven runs."""
+    (est, conv, iters), runs, _ = aewa_runs
+    conv_k = np.stack([r[1] for r in runs])                     # (11, B)
+    assert (conv == conv_k.any(axis=0)).all()
+    first = np.where(conv_k.any(axis=0), conv_k.argmax(axis=0), 10)
+    for b in range(est.shape[0]):
+        e_k, _, it_k = runs[first[b]]
+        assert (est[b] == e_k[b]).all() and iters[b] == it_k[b], b
+    # the schedule is needed: some shots converge only at alpha < 1, and
+    # at smaller alpha than EWAInit's usual 0.5 too
+    assert (first > 0).any() and (first[conv] > 5).any()
+
+
+def test_aewa_first_attempt_is_plain_bp(aewa_runs):
+    """At alpha = 1, Pi^(t) = Pi^(0) (eq. (EWAInit)), i.e. LLR-BP4: where
+    plain BP converges AEWA-BP returns its result exactly."""
+    (est, conv, iters), _, (est_p, conv_p, iters_p) = aewa_runs
+    assert conv[conv_p].all()
+    assert (est[conv_p] == est_p[conv_p]).all() and (iters[conv_p] == iters_p[conv_p]).all()
+    assert conv.mean() > conv_p.mean()
