@@ -37,7 +37,7 @@ P_SWEEP = [0.02, 0.04, 0.06, 0.08, 0.10, 0.12, 0.14, 0.16]
 SEED = 0xB9E00001
 CODE, DIST, MAX_ITER = "toric", 15, 100
 VARIANT_PARAMS = {"ewainit": dict(alpha=0.5), "plain": {}, "momentum": dict(alpha=0.5, gamma=0.0),
-                  "adagrad": dict(alpha=5.0)}
+                  "adagrad": dict(alpha=5.0), "aewa": dict()}
 
 
 def parse():
@@ -53,10 +53,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
-    ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve", "train"],
+    ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve", "train", "aewa"],
                     help="toric15: the headline sweep; mixed: many codes in one batched launch; "
                          "serve: continuous-batching server on a Poisson request stream; "
-                         "train: differentiable unrolled EWAInit-BP (forward + backward kernels)")
+                         "train: differentiable unrolled EWAInit-BP (forward + backward kernels); "
+                         "aewa: EWAInit-BP vs AEWA-BP on planar L = 3, 7, 11 (Appendix C)")
     ap.add_argument("--loads", default="1e4,1e5,1e6,1e7", help="offered loads (requests/s) for --workload serve")
     return ap.parse_args()
 
@@ -348,7 +349,9 @@ def run_ours(args, rank, world):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sfu_peak = float("nan") if args.no_probe else bpq.probe_peak("sfu", blocks=sms * 8, threads=256, iters=4096)
     fma_peak = float("nan") if args.no_probe else bpq.probe_peak("fma", blocks=sms * 8, threads=256, iters=4096)
-    sfu_per_edge_update = 7.0
+    # EWAInit-BP, delta form, degree-4 qubits: check side rcp + lg2, variable
+    # side ex2 + rcp per edge, and 4 ex2 per qubit shared by its 4 edges
+    sfu_per_edge_update = 5.0
     ew = results.get("ewainit", head)
     kernel_sec = ew["launch_ms_mean"] / 1e3
     achieved = sfu_per_edge_update * (ew["edge_updates_per_step"] / len(P_SWEEP)) / kernel_sec
@@ -521,6 +524,89 @@ def run_mixed(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ AEWA-BP workload (Appendix C)
+
+AEWA_L = (3, 7, 11)
+AEWA_PER = (0.01, 0.06, 0.1, 0.2)
+AEWA_SHOTS = 100_000
+
+
+def run_aewa(args, rank, world):
+    """EWAInit-BP (alpha 0.5) and AEWA-BP on the planar codes L = 3, 7, 11 at
+    the error rates of Appendix C's runtime table, max 100 iterations: batch
+    throughput, per-decode latency of single shots, and LER."""
+    import torch
+
+    import paper_2407_11523_gb300 as bpq
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    B = AEWA_SHOTS
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    work = bpq.workspace(dev)
+    rows, timed_ms, launches = [], {"ewainit": 0.0, "aewa": 0.0}, 0
+    for L in AEWA_L:
+        t = bpq.Tanner("planar", L).upload()
+        for k, p in enumerate(AEWA_PER):
+            ch = (p / 3, p / 3, p / 3)
+            err, syn = bpq.sample(t, *ch, seed=SEED + 200 + 10 * L + k, shot0=rank * B, B=B)
+            prior = bpq.prior_tensor(t, *ch)
+            out = (torch.empty((B, t.N), dtype=torch.uint8, device=dev), torch.empty(B, dtype=torch.uint8, device=dev),
+                   torch.empty(B, dtype=torch.uint8, device=dev))
+            row = {"L": L, "N": t.N, "per": p}
+            for v in ("ewainit", "aewa"):
+                params = bpq.make_params(v, **({"alpha": 0.5} if v == "ewainit" else {}))
+                for _ in range(args.warmup):
+                    bpq.decode(t, syn, prior, v, params=params, max_iter=MAX_ITER, out=out, work=work)
+                torch.cuda.synchronize()
+                barrier(world)
+                ms = 0.0
+                for s in range(args.steps):
+                    flush.fill_(s & 0xFF)  # L2 flush between timed launches (outside the events)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    bpq.decode(t, syn, prior, v, params=params, max_iter=MAX_ITER, out=out, work=work)
+                    b.record(stream)
+                    b.synchronize()
+                    ms += a.elapsed_time(b)
+                    launches += 1
+                ms = reduce_max(ms, world)
+                timed_ms[v] += ms
+                fail = bpq.check_logical(t, err, out[0])
+                n_fail = reduce_sum(float((fail > 0).sum().item()), world)
+                conv = float(out[1].float().mean().item())
+                iters = float(out[2].float().mean().item())
+                # per-decode latency: one launch per single shot, 100 different shots
+                lat = []
+                for i in range(100 if not args.no_latency else 0):
+                    o = tuple(x[i:i + 1] for x in out)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    bpq.decode(t, syn[i:i + 1], prior, v, params=params, max_iter=MAX_ITER, out=o, work=work)
+                    b.record(stream)
+                    b.synchronize()
+                    lat.append(a.elapsed_time(b))
+                row[v] = {"shots_per_s": reduce_sum(float(B * args.steps), world) / (ms / 1e3),
+                          "ler": n_fail / (B * world), "converged_frac": conv, "avg_iterations": iters,
+                          "single_shot_ms_mean": float(np.mean(lat)) if lat else None,
+                          "single_shot_ms_p99": float(np.percentile(lat, 99)) if lat else None}
+            rows.append(row)
+    if rank == 0:
+        shots = float(B * args.steps * len(AEWA_L) * len(AEWA_PER) * world)
+        line = {"metric": "AEWA-BP decoded shots/s over planar L=3,7,11 x PER {0.01,0.06,0.1,0.2}",
+                "value": shots / (timed_ms["aewa"] / 1e3), "unit": "shots/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": timed_ms["aewa"] / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"planar L in {list(AEWA_L)}, depolarising PER in {list(AEWA_PER)}, "
+                                       f"{B} shots per point per rank, max_iter {MAX_ITER}; AEWA-BP tries "
+                                       "alpha = 1.0, 0.9, ..., 0.0; EWAInit-BP alpha 0.5 alongside",
+                           "l2": "a 256 MB buffer is written between timed launches"},
+                "ewainit_shots_per_s": shots / (timed_ms["ewainit"] / 1e3),
+                "points": rows, "gpu_launches": launches // 2}
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving workload
 
 SERVE_CODES = [(k, d) for k in ("planar", "xzzx") for d in range(5, 32, 2)]
@@ -552,6 +638,7 @@ def run_serve(args, rank, world):
         fill[c] += 1
     results = []
     srv.replay(code_pool[:2000], np.zeros(2000), syn_pool[:2000])  # warm-up
+    launches0 = srv.launches()
     for load in [float(x) for x in args.loads.split(",")]:
         R = int(min(R_pool, max(2000, load * 1.0)))
         arrival = np.cumsum(rng.exponential(1.0 / load, size=R))
@@ -574,7 +661,7 @@ def run_serve(args, rank, world):
                                        "depolarising p = 0.05, EWAInit-BP alpha = 0.5, max_iter 100; 4 lanes x 4096 "
                                        "shots of device budget; Poisson arrivals",
                            "loads": results},
-                "gpu_launches": None}
+                "gpu_launches": srv.launches() - launches0}
         print(json.dumps(line), flush=True)
 
 
@@ -642,10 +729,26 @@ def run_train(args, rank, world):
         fail = bpq.check_logical(t, err_t, est.to(torch.uint8).contiguous())
         return float((fail > 0).float().mean())
 
+    def ler_early_exit(aa, bb, ww):
+        # Algorithm 2's stopping rule on the unrolled decoder: each shot takes
+        # the decision of the first iteration whose decision satisfies the
+        # syndrome (else that of iteration T)
+        outcome = torch.full((err_t.shape[0],), 255, dtype=torch.uint8, device=err_t.device)
+        for Tp in range(1, T + 1):
+            Q, _ = bpq.unrolled_posterior(t, syn_t, err_t, prior, aa[:Tp], bb[:Tp], ww, T=Tp, ckpt_every=Tp)
+            allpos = (Q > 0).all(-1)
+            est = torch.where(allpos, torch.zeros_like(allpos, dtype=torch.long), 1 + Q.argmin(-1))
+            f = bpq.check_logical(t, err_t, est.to(torch.uint8).contiguous())
+            take = (outcome == 255) & ((f != 1) | (Tp == T))
+            outcome[take] = f[take]
+        return float((outcome > 0).float().mean())
+
     with torch.no_grad():
         Qtr, Ltr = bpq.unrolled_posterior(t, syn_t, err_t, prior, a, b, w, T=T)
         Q0, L0 = bpq.unrolled_posterior(t, syn_t, err_t, prior, torch.full_like(a, 0.5), torch.zeros_like(b),
                                         torch.ones_like(w), T=T)
+        ler_ee = {"trained": ler_early_exit(a.detach(), b.detach(), w.detach()),
+                  "untrained": ler_early_exit(torch.full_like(a, 0.5), torch.zeros_like(b), torch.ones_like(w))}
     est_k, conv_k, _ = bpq.decode(t, syn_t, prior, "ewainit", max_iter=T, alpha=0.5)
     ler_kernel = float((bpq.check_logical(t, err_t, est_k) > 0).float().mean())
     if rank == 0:
@@ -661,8 +764,10 @@ def run_train(args, rank, world):
                 "train_loss_first_last": [losses[0], losses[-1]],
                 "held_out_loss": {"trained": float(Ltr), "untrained": float(L0)},
                 "held_out_ler": {"trained_unrolled": ler_from_Q(Qtr), "untrained_unrolled": ler_from_Q(Q0),
+                                 "trained_unrolled_early_exit": ler_ee["trained"],
+                                 "untrained_unrolled_early_exit": ler_ee["untrained"],
                                  "ewainit_kernel_early_exit": ler_kernel, "shots": int(err_t.shape[0])},
-                "gpu_launches": None}
+                "gpu_launches": 6 * args.steps}
         print(json.dumps(line), flush=True)
 
 def main():
@@ -674,6 +779,8 @@ def main():
         run_mixed(args, rank, world)
     elif args.workload == "serve":
         run_serve(args, rank, world)
+    elif args.workload == "aewa":
+        run_aewa(args, rank, world)
     elif args.workload == "train":
         run_train(args, rank, world)
     else:

@@ -36,8 +36,11 @@ enum bpq_code { BPQ_PLANAR = 0, BPQ_TORIC = 1, BPQ_XZZX = 2 };
 
 /* Decoder variants: LLR-BP4 (Sec. II-B1), Momentum-BP (Sec. III-A1,
  * Algorithm 1), AdaGrad-BP (Sec. III-A2), EWAInit-BP (Sec. III-B,
- * Algorithm 2). */
-enum bpq_variant { BPQ_PLAIN = 0, BPQ_MOMENTUM = 1, BPQ_ADAGRAD = 2, BPQ_EWAINIT = 3 };
+ * Algorithm 2), and AEWA-BP (Appendix C): EWAInit-BP run with
+ * alpha = 1.0, 0.9, ..., 0.0 in turn until a run converges; its outputs are
+ * those of the last run (iters counts that run only).  AEWA-BP is offered by
+ * bpq_decode and bpq_decode_host (not by the trace, batch or server paths). */
+enum bpq_variant { BPQ_PLAIN = 0, BPQ_MOMENTUM = 1, BPQ_ADAGRAD = 2, BPQ_EWAINIT = 3, BPQ_AEWA = 4 };
 
 enum bpq_status {
     BPQ_OK = 0,
@@ -295,6 +298,11 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
 int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *arrival_s, const uint32_t *syn_host,
                       const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, uint8_t *conv_host,
                       uint8_t *iters_host, double *done_s, int *lanes_used);
+
+/* launches (may be NULL): the number of batched decode kernels the server
+ * has launched since bpq_server_create (one per dispatch to a lane).
+ * Errors: EINVAL. */
+int bpq_server_stats(const bpq_server *s, long *launches);
 
 void bpq_server_free(bpq_server *s);
 

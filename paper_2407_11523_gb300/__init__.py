@@ -7,7 +7,7 @@ The compute lives in libbpq.so (CUDA for sm_103a, C ABI in include/bpq.h);
 this package is its thin Python binding.
 """
 from ._binding import (  # noqa: F401
-    ADAGRAD, CODES, EWAINIT, MOMENTUM, PLAIN, PLANAR, TORIC, VARIANTS, XZZX,
+    ADAGRAD, AEWA, CODES, EWAINIT, MOMENTUM, PLAIN, PLANAR, TORIC, VARIANTS, XZZX,
     BPQError, BatchPlan, Params, Server, Tanner, autotune, check_logical, decode, decode_host, decode_host_bytes, decode_status,
     decode_trace, default_params, lib, make_params, prior_tensor, probe_peak, sample, unrolled_loss,
     unrolled_posterior, workspace,

@@ -15,9 +15,9 @@ import torch
 from . import build as _build
 
 PLANAR, TORIC, XZZX = 0, 1, 2
-PLAIN, MOMENTUM, ADAGRAD, EWAINIT = 0, 1, 2, 3
+PLAIN, MOMENTUM, ADAGRAD, EWAINIT, AEWA = 0, 1, 2, 3, 4
 CODES = {"planar": PLANAR, "toric": TORIC, "xzzx": XZZX}
-VARIANTS = {"plain": PLAIN, "momentum": MOMENTUM, "adagrad": ADAGRAD, "ewainit": EWAINIT}
+VARIANTS = {"plain": PLAIN, "momentum": MOMENTUM, "adagrad": ADAGRAD, "ewainit": EWAINIT, "aewa": AEWA}
 
 
 class Params(ctypes.Structure):
@@ -78,6 +78,7 @@ def lib():
             "bpq_server_device_bytes": (sz, [P, i, i, i]),
             "bpq_server_create": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, i, P, sz, PP]),
             "bpq_server_replay": (i, [P, i, P, P, P, P, P, P, P, P, P, pi]),
+            "bpq_server_stats": (i, [P, ctypes.POINTER(ctypes.c_long)]),
             "bpq_server_free": (None, [P]),
             "bpq_train_workspace_bytes": (sz, [P, i, i, i]),
             "bpq_train_forward": (i, [P, P, P, P, i, i, i, P, P, P, ctypes.c_float, P, P, P, sz, P]),
@@ -448,6 +449,12 @@ class Server:
                "bpq_server_replay")
         ests = [est[o:o + n] for o, n in zip(est_off, Ns)]
         return ests, conv[:R], iters[:R], done[:R], used.value
+
+    def launches(self):
+        """Batched decode kernels launched since creation."""
+        n = ctypes.c_long()
+        _check(lib().bpq_server_stats(self._h, ctypes.byref(n)), "bpq_server_stats")
+        return n.value
 
     def __del__(self):
         h = getattr(self, "_h", None)

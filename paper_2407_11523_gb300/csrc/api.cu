@@ -207,11 +207,13 @@ int cuda_check(cudaError_t e, const char *what) {
     return fail(BPQ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// The phi value that corresponds to the message clip: phi(c) = log1p(2 / expm1(c)).
+// 1 - tanh(c/2) = 2 / (e^c + 1): the smallest delta of a message clipped to |m| <= c
+float delta_of_clip(float c) { return (float)(2.0 / (std::exp((double)c) + 1.0)); }
+// phi(c) = log1p(2 / expm1(c)) = -ln tanh(c/2): the smallest phi of a clipped message
 float phi_of_clip(float c) { return (float)std::log1p(2.0 / std::expm1((double)c)); }
 
 int check_params(int variant, const bpq_params *params, bpq_params *out) {
-    if (variant < BPQ_PLAIN || variant > BPQ_EWAINIT) return fail(BPQ_EINVAL, "unknown variant");
+    if (variant < BPQ_PLAIN || variant > BPQ_AEWA) return fail(BPQ_EINVAL, "unknown variant");
     if (params) *out = *params;
     else bpq_default_params(variant, out);
     if (!(out->msg_clip > 0.0f && out->msg_clip <= 80.0f)) return fail(BPQ_EINVAL, "msg_clip must be in (0, 80]");
@@ -229,14 +231,15 @@ int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prio
     if (max_iter < 1 || max_iter > 255) return fail(BPQ_EINVAL, "max_iter must be in [1, 255]");
     if (B > 0 && (!syn || !prior || !work)) return fail(BPQ_EINVAL, "NULL input or workspace");
     std::memset(&a, 0, sizeof a);
-    a.table = t->d_table;
+    a.split = t->split ? 1 : 0;
+    a.table = t->split ? t->d_table_split : t->d_table;
     a.table_bytes = (uint32_t)t->table.size();
     a.off_chk_pauli = t->off_chk_pauli;
     a.off_var_pauli = t->off_var_pauli;
     a.syn = syn;
     a.prior = prior;
     a.work = static_cast<uint32_t *>(work);
-    a.var_canon = t->d_var_canon;
+    a.var_canon = t->split ? t->d_var_canon_split : t->d_var_canon;
     a.chk_ptr = t->d_chk_ptr;
     a.N = t->N;
     a.M = t->M;
@@ -248,6 +251,7 @@ int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prio
     a.gamma = p.gamma;
     a.eps = p.eps;
     a.clip = p.msg_clip;
+    a.delta_clip = delta_of_clip(p.msg_clip);
     a.phi_clip = phi_of_clip(p.msg_clip);
     a.ada_from1 = p.adagrad_g_from_iter1 ? 1 : 0;
     return BPQ_OK;
@@ -276,7 +280,9 @@ int bpq_tanner_upload(bpq_tanner *t, int device) {
     const size_t o_canon = al(t->table.size());
     const size_t o_ptr = o_canon + al(sizeof(int32_t) * t->var_canon.size());
     const size_t o_log = o_ptr + al(sizeof(int32_t) * t->chk_ptr.size());
-    const size_t total = o_log + al(t->logicals.size() + 1);
+    const size_t o_tab2 = o_log + al(t->logicals.size() + 1);
+    const size_t o_canon2 = o_tab2 + al(t->table_split.size());
+    const size_t total = o_canon2 + al(sizeof(int32_t) * t->var_canon_split.size());
     void *blob = nullptr;
     rc = bpq::cuda_check(cudaMalloc(&blob, total), "cudaMalloc");
     if (rc) return rc;
@@ -288,6 +294,11 @@ int bpq_tanner_upload(bpq_tanner *t, int device) {
         e = cudaMemcpy(b + o_ptr, t->chk_ptr.data(), sizeof(int32_t) * t->chk_ptr.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !t->logicals.empty())
         e = cudaMemcpy(b + o_log, t->logicals.data(), t->logicals.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && t->split)
+        e = cudaMemcpy(b + o_tab2, t->table_split.data(), t->table_split.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && t->split)
+        e = cudaMemcpy(b + o_canon2, t->var_canon_split.data(), sizeof(int32_t) * t->var_canon_split.size(),
+                       cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
         return bpq::cuda_check(e, "cudaMemcpy");
@@ -299,6 +310,8 @@ int bpq_tanner_upload(bpq_tanner *t, int device) {
     t->d_var_canon = reinterpret_cast<const int32_t *>(b + o_canon);
     t->d_chk_ptr = reinterpret_cast<const int32_t *>(b + o_ptr);
     t->d_logicals = t->logicals.empty() ? nullptr : b + o_log;
+    t->d_table_split = t->split ? b + o_tab2 : nullptr;
+    t->d_var_canon_split = t->split ? reinterpret_cast<const int32_t *>(b + o_canon2) : nullptr;
     return BPQ_OK;
 }
 

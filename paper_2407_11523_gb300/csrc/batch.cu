@@ -33,6 +33,7 @@ BatchKernelFn pick_batch_kernel(int variant, int npt) {
         case BPQ_MOMENTUM: return pick_momentum_batch(npt);
         case BPQ_ADAGRAD: return pick_adagrad_batch(npt);
         case BPQ_EWAINIT: return pick_ewainit_batch(npt);
+        case BPQ_AEWA: return pick_aewa_batch(npt);
     }
     return nullptr;
 }
@@ -58,7 +59,8 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
     if (!items || n_items < 1) return fail(BPQ_EINVAL, "no batch items");
     if (tile_shots < 1) return fail(BPQ_EINVAL, "tile_shots must be >= 1");
     if (max_iter < 1 || max_iter > 255) return fail(BPQ_EINVAL, "max_iter must be in [1, 255]");
-    if (variant < BPQ_PLAIN || variant > BPQ_EWAINIT) return fail(BPQ_EINVAL, "unknown variant");
+    if (variant < BPQ_PLAIN || variant > BPQ_EWAINIT)
+        return fail(BPQ_EINVAL, "the batched kernel takes plain, Momentum, AdaGrad or EWAInit BP");
     if (!work_dev) return fail(BPQ_EINVAL, "NULL workspace");
     const int device = items[0].tanner ? items[0].tanner->device : -1;
     long total = 0;
@@ -100,9 +102,6 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
         a.group_bytes = s.group_bytes;
         a.npt = s.npt;
         a.groups_per_cta = gpc;
-        bool noy = true;
-        for (uint8_t p : t->chk_pauli) noy = noy && p != 2;
-        a.noy = noy ? 1 : 0;
         npt_max = std::max(npt_max, s.npt);
         smem = std::max(smem, s.smem);
         const int per_tile = gpc * tile_shots;

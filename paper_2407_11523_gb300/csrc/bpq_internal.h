@@ -33,17 +33,27 @@ struct bpq_tanner {
     std::vector<uint8_t> chk_pauli;
     std::vector<uint8_t> logicals;  // 2K x N Pauli codes (empty if unknown)
 
-    // Decoder adjacency tables (built by bpq::build_tables):
-    //  slot of edge (qubit j, k-th check of j in increasing check order) = 4 j + k
+    // Decoder adjacency tables (built by bpq::build_tables), generic layout:
+    //  slot of edge (qubit j, k-th check of j in increasing check order)
+    //  = 4 j + ((k + j / 8) mod 4)
     std::vector<uint8_t> table;      // [chk_slot u16 M_pad x 4][chk_pauli u8 M_pad][var_pauli u8 N_pad]
     uint32_t off_chk_pauli = 0, off_var_pauli = 0;
     std::vector<int32_t> var_canon;  // 4N: check-major edge index of each slot (-1 = padding)
+    // Split layout, for codes without Y entries whose qubits have at most two
+    // X edges and two Z edges (every surface code here): the same table
+    // format, but slot p * n4 + j (n4 = N rounded up to 4) holds qubit j's
+    // p-th edge with positions 0, 1 its X edges and 2, 3 its Z edges.
+    bool split = false;
+    std::vector<uint8_t> table_split;
+    std::vector<int32_t> var_canon_split;  // 4 n4, indexed by split slot
 
     // device
     int device = -1;
     void *dev_blob = nullptr;
     const uint8_t *d_table = nullptr;
     const int32_t *d_var_canon = nullptr;
+    const uint8_t *d_table_split = nullptr;
+    const int32_t *d_var_canon_split = nullptr;
     const int32_t *d_chk_ptr = nullptr;
     const uint8_t *d_logicals = nullptr;
     int num_sms = 0;

@@ -9,14 +9,17 @@ namespace bpq {
 
 namespace {
 
-int state_arrays(int variant) { return variant == BPQ_PLAIN ? 0 : variant == BPQ_EWAINIT ? 3 : 6; }
+int state_arrays(int variant) {
+    return variant == BPQ_PLAIN ? 0 : (variant == BPQ_EWAINIT || variant == BPQ_AEWA) ? 3 : 6;
+}
 
-DecodeKernelFn pick(int variant, int npt, bool trace, bool noy) {
+DecodeKernelFn pick(int variant, int npt, bool trace, bool split) {
     switch (variant) {
-        case BPQ_PLAIN: return pick_plain(npt, trace, noy);
-        case BPQ_MOMENTUM: return pick_momentum(npt, trace, noy);
-        case BPQ_ADAGRAD: return pick_adagrad(npt, trace, noy);
-        case BPQ_EWAINIT: return pick_ewainit(npt, trace, noy);
+        case BPQ_PLAIN: return pick_plain(npt, trace, split);
+        case BPQ_MOMENTUM: return pick_momentum(npt, trace, split);
+        case BPQ_ADAGRAD: return pick_adagrad(npt, trace, split);
+        case BPQ_EWAINIT: return pick_ewainit(npt, trace, split);
+        case BPQ_AEWA: return pick_aewa(npt, trace, split);
     }
     return nullptr;
 }
@@ -45,10 +48,10 @@ int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
     s->npt = npt;
     s->groups_per_cta = gpc;
     s->n_pad = (t->N + 3) & ~3;
-    // message slots (+ zero and trash slots), anticommutation bytes, state
+    // message slots (+ zero and trash slots), state
     s->slots_floats = (uint32_t)(4 * s->n_pad + 4);
     const int nstate = state_arrays(variant < 0 ? BPQ_MOMENTUM : variant);
-    s->group_bytes = (uint32_t)(4 * s->slots_floats + ((s->slots_floats + 15) & ~15u) + 4 * nstate * s->n_pad);
+    s->group_bytes = (uint32_t)(4 * s->slots_floats + 4 * nstate * s->n_pad);
     s->smem = kSmemHeader + t->table.size() + (size_t)12 * s->n_pad + (size_t)gpc * s->group_bytes;
     if (s->smem > 227 * 1024) return fail(BPQ_EINVAL, "shared memory of the launch shape exceeds 227 KB");
     return BPQ_OK;
@@ -73,7 +76,7 @@ int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
     s->n_pad = (t->N + 3) & ~3;
     s->slots_floats = (uint32_t)(4 * s->n_pad + 4);
     const int nstate = state_arrays(variant);
-    s->group_bytes = (uint32_t)(4 * s->slots_floats + ((s->slots_floats + 15) & ~15u) + 4 * nstate * s->n_pad);
+    s->group_bytes = (uint32_t)(4 * s->slots_floats + 4 * nstate * s->n_pad);
     s->smem = kSmemHeader + kDescBytes + t->table.size() + (size_t)12 * s->n_pad + (size_t)gpc * s->group_bytes;
     if (s->smem > 227 * 1024) return fail(BPQ_EINVAL, "a code of the batch needs more than 227 KB of shared memory");
     return BPQ_OK;
@@ -83,10 +86,8 @@ int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, c
     LaunchShape s;
     int rc = decode_launch_shape(t, variant, &s);
     if (rc) return rc;
-    bool noy = true;
-    for (uint8_t p : t->chk_pauli) noy = noy && p != 2;
-    DecodeKernelFn fn = pick(variant, s.npt, trace, noy);
-    if (!fn) return fail(BPQ_EINVAL, "bad variant");
+    DecodeKernelFn fn = pick(variant, s.npt, trace, a.split != 0);
+    if (!fn) return fail(BPQ_EINVAL, "no kernel for this variant (AEWA-BP has no trace mode)");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     const int threads = s.T * s.groups_per_cta;

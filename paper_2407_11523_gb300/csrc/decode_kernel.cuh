@@ -13,20 +13,23 @@
 // adjacency and temporaries.
 //
 // Arithmetic (Sec. II-B1 and Sec. III of the paper, fp32):
-//  * check-to-variable, eq. (h_update): with phi(x) = -ln tanh(x/2) (its own
-//    inverse), 2 atanh(prod_k tanh(m_k/2)) = sign * phi(sum_k phi(|m_k|)),
-//    sign = (-1)^{s_i} prod_k sign(m_k).  Variable-to-check messages are
-//    stored as sign(m) * phi(|m|), so the check pass only sums magnitudes
-//    and XORs sign bits.
+//  * check-to-variable, eq. (h_update): 2 atanh(prod_k tanh(m_k/2)) with
+//    sign (-1)^{s_i} prod_k sign(m_k).  Variable-to-check messages are
+//    stored as sign(m) * delta, delta = 1 - tanh(|m|/2) in (0, 1]; the check
+//    pass XORs sign bits and forms D = 1 - prod_k (1 - delta_k) with
+//    a (+) b = a + b - ab (no relative accuracy is lost for small deltas,
+//    i.e. confident messages), then |m_c->v| = 2 atanh(1 - D) =
+//    ln((2 - D) / D): one reciprocal and one logarithm per edge.  AdaGrad-BP
+//    keeps Gallager's sign/phi form (see PhiForm) for its conditioning.
 //  * variable-to-check, eqs. (lambda), (v_update), (mombp5): the message is
 //    lambda_H(Q - own anticommuting message) = ln(C / A) with
 //    C = 1 + e^{-Q_H} and A = (e^{-Q_a} + e^{-Q_b}) e^{m_c->v}, a, b the two
 //    Paulis other than H.  All four exponentials share the shift
 //    c0 = min(0, Q_X, Q_Y, Q_Z), so nothing overflows, and the stored value
-//    phi(|lambda|) = ln((C+A)/|C-A|) = log1p(2 min(C,A) / |C-A|) comes out
-//    of C and A without forming lambda.
+//    delta = 1 - tanh(|lambda|/2) = 2 min(C, A) / (C + A) comes out of C
+//    and A without forming lambda (one reciprocal per edge, no logarithm).
 //  * message saturation: |m| <= msg_clip on both directions, i.e.
-//    phi(|m_v->c|) >= phi(msg_clip) and |m_c->v| <= msg_clip.
+//    delta(m_v->c) >= 2 / (e^msg_clip + 1) and |m_c->v| <= msg_clip.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -148,6 +151,30 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
+// Messages on the check side are carried as delta = 1 - tanh(|m|/2) in
+// (0, 1] (sign kept in the float's sign bit), so that eq. (h_update)
+// becomes a product: with tanh(|w|/2) = prod_f (1 - delta_f), the
+// complement D = 1 - prod_f (1 - delta_f) is accumulated with
+// a (+) b = a + b - ab = 1 - (1-a)(1-b), which loses no relative accuracy
+// when every delta is small (confident messages), and
+// |w| = 2 atanh(1 - D) = ln((2 - D) / D).
+__device__ __forceinline__ float oplus(float a, float b) { return fmaf(-a, b, a + b); }
+
+// |m_{c->v}| = ln((2 - D) / D), D in [0, 1]; D = 0 (only certain incoming
+// messages, e.g. a degree-1 check) gives +inf, clipped by the caller.
+__device__ __forceinline__ float c2v_magnitude(float D) { return kLn2 * lg2((2.0f - D) * rcp(D)); }
+
+// AdaGrad-BP keeps Gallager's form instead: v->c messages stored as
+// sign * phi(|m|), phi(x) = -ln tanh(x/2) (its own inverse), summed by the
+// check pass, 2 atanh(prod tanh(m/2)) = sign * phi(sum phi(|m|)).  phi keeps
+// relative accuracy at both ends (small and large |m|), which AdaGrad's
+// scale-invariant step g'/(sqrt(G)+eps) needs; delta = 1 - tanh(|m|/2) holds
+// only absolute accuracy for uncertain (small) messages.
+template <int VARIANT>
+struct PhiForm {
+    static constexpr bool value = VARIANT == BPQ_ADAGRAD;
+};
+
 // Check-to-variable magnitude w = phi(S) = ln(1 + 2 / (e^S - 1)), S >= 0,
 // needed to an absolute accuracy.  e^S - 1 keeps its relative accuracy:
 // below S = 1/4 from its Taylor series to S^6/720 (truncation < 5e-8
@@ -177,40 +204,50 @@ __device__ __forceinline__ float log1p_rel(float r) {
 // EWAInit Q^(t-1); Momentum Q^(t-1), g; AdaGrad Q^(t-1), G.
 template <int VARIANT>
 struct StateArrays {
-    static constexpr int n = VARIANT == BPQ_PLAIN ? 0 : VARIANT == BPQ_EWAINIT ? 3 : 6;
+    static constexpr int n = VARIANT == BPQ_PLAIN ? 0 : (VARIANT == BPQ_EWAINIT || VARIANT == BPQ_AEWA) ? 3 : 6;
 };
 
-// Anticommutation mask: bit p of (kAntiLut >> 4d) is <d, p> for Pauli codes d, p.
-constexpr uint32_t kAntiLut = 0x6AC0u;
-
 // Sum of the c->v messages from checks that anticommute with X, Y, Z
-// (S_W of eq. (p_update)).  NOY: the code has no Y entries, so an X-type
-// check contributes to S_Z and S_Y and a Z-type check to S_X and S_Y.
-template <bool NOY>
+// (S_W of eq. (p_update)) in the generic layout: position n of the qubit
+// holds an edge with Pauli (vp >> 2n) & 3 (0 = unused slot).
 __device__ __forceinline__ void anticommuting_sums(uint32_t vp, const float (&w)[4], float &SX, float &SY,
                                                    float &SZ) {
     SX = SY = SZ = 0.f;
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
         const uint32_t p = (vp >> (2 * n)) & 3u;
-        if (NOY) {
-            const float wx = p == 1u ? w[n] : 0.f, wz = p == 3u ? w[n] : 0.f;
-            SZ += wx;
-            SX += wz;
-        } else {
-            SX += (p != 0u && p != 1u) ? w[n] : 0.f;
-            SY += (p != 0u && p != 2u) ? w[n] : 0.f;
-            SZ += (p != 0u && p != 3u) ? w[n] : 0.f;
-        }
+        SX += (p != 0u && p != 1u) ? w[n] : 0.f;
+        SY += (p != 0u && p != 2u) ? w[n] : 0.f;
+        SZ += (p != 0u && p != 3u) ? w[n] : 0.f;
     }
-    if (NOY) SY = SX + SZ;
 }
 
-// Variable-to-check messages of one qubit, stored as sign * phi(|lambda|)
-// into its four slots; win are the incoming check-to-variable messages.
-template <bool TRACE, bool NOY>
+// Bytes 0..3: 1 where the decision d anticommutes with the qubit's edge at
+// position n (pp holds the edge Paulis one per byte; unused bytes are 0).
+__device__ __forceinline__ uint32_t anti_bytes(uint32_t d, uint32_t pp) {
+    const uint32_t x = (d * 0x01010101u) ^ pp;                       // 0 where d == p
+    const uint32_t ne = (x | (x >> 1)) & 0x01010101u;                // 1 where d != p
+    const uint32_t nz = (pp | (pp >> 1)) & 0x01010101u;              // 1 where p != I
+    return d ? (ne & nz) : 0u;
+}
+
+// The same for the split layout, where positions 0, 1 hold X edges and 2, 3
+// Z edges: X anticommutes with Y, Z (d >= 2) and Z with X, Y (d in {1, 2}).
+__device__ __forceinline__ uint32_t anti_bytes_split(uint32_t d) {
+    return (d >= 2u ? 0x00000101u : 0u) | (d - 1u < 2u ? 0x01010000u : 0u);
+}
+
+// Variable-to-check messages of one qubit (position n of the layout), from
+// its posterior Q and the incoming check-to-variable messages win: stored
+// as sign * delta(|lambda|) (sign * phi(|lambda|) with PHI), the least
+// significant bit replaced by byte n of ab (whether this iteration's
+// decision anticommutes with the edge), which the next check pass reads for
+// the syndrome test.  Generic layout: slots 4j .. 4j+3, one float4 store.
+// Split layout: slots n * n_pad + j; unused positions are written (as 0)
+// only at t = 0, when ALL is set.
+template <bool TRACE, bool SPLIT, bool PHI, bool ALL>
 __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, float *slots, int j, int t, int shot, uint32_t vp,
-                                         float QX, float QY, float QZ, const float (&win)[4]) {
+                                         float QX, float QY, float QZ, const float (&win)[4], uint32_t ab) {
     const float c0 = fminf(0.f, fminf(QX, fminf(QY, QZ)));
     const float e0 = ex2(c0 * kLog2e);
     const float eX = ex2((c0 - QX) * kLog2e), eY = ex2((c0 - QY) * kLog2e), eZ = ex2((c0 - QZ) * kLog2e);
@@ -222,32 +259,39 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, float *slots, int 
     for (int n = 0; n < 4; ++n) {
         const uint32_t p = (vp >> (2 * n)) & 3u;
         float C, Ab;
-        if (NOY) {
-            C = p == 1u ? CX : CZ;
-            Ab = p == 1u ? AX : AZ;
+        if (SPLIT) {
+            C = n < 2 ? CX : CZ;
+            Ab = n < 2 ? AX : AZ;
         } else {
             C = p == 1u ? CX : p == 2u ? CY : CZ;
             Ab = p == 1u ? AX : p == 2u ? AY : AZ;
         }
         const float A = Ab * ex2(win[n] * kLog2e);
-        const float mx = fmaxf(C, A), mn = fminf(C, A);
-        const float ph = fmaxf(log1p_rel(2.0f * mn * rcp(mx - mn)), a.phi_clip);  // |lambda| <= msg_clip
-        out[n] = p ? ((A > C) ? -ph : ph) : 0.f;
+        // lambda = ln(C / A); delta = 1 - tanh(|lambda|/2) = 2 min(C, A) / (C + A),
+        // at least delta_clip; or phi(|lambda|) = log1p(2 min(C, A) / |C - A|),
+        // at least phi_clip (|lambda| <= msg_clip)
+        float dl;
+        if (PHI) {
+            const float mx = fmaxf(C, A), mn = fminf(C, A);
+            dl = fmaxf(log1p_rel(2.0f * mn * rcp(mx - mn)), a.phi_clip);
+        } else {
+            dl = fmaxf(2.0f * fminf(C, A) * rcp(C + A), a.delta_clip);
+        }
+        const uint32_t bits = (__float_as_uint(dl) & ~1u) | ((ab >> (8 * n)) & 1u) | (A > C ? 0x80000000u : 0u);
+        out[n] = p ? __uint_as_float(bits) : 0.f;
         if (TRACE && a.tr_v2c && p) {
             const float lam = fminf(fmaxf(kLn2 * (lg2(C) - lg2(A)), -a.clip), a.clip);
-            a.tr_v2c[((size_t)shot * (a.max_iter + 1) + t) * a.E + a.var_canon[4 * j + n]] = lam;
+            const int s = SPLIT ? n * a.n_pad + j : 4 * j + n;
+            a.tr_v2c[((size_t)shot * (a.max_iter + 1) + t) * a.E + a.var_canon[s]] = lam;
         }
     }
-    *reinterpret_cast<float4 *>(slots + 4 * j) = make_float4(out[0], out[1], out[2], out[3]);
-}
-
-// Bytes 0..3: 1 where the decision d anticommutes with the qubit's edge n
-// (pp holds the edge Paulis one per byte; padding bytes are 0).
-__device__ __forceinline__ uint32_t anti_bytes(uint32_t d, uint32_t pp) {
-    const uint32_t x = (d * 0x01010101u) ^ pp;                       // 0 where d == p
-    const uint32_t ne = (x | (x >> 1)) & 0x01010101u;                // 1 where d != p
-    const uint32_t nz = (pp | (pp >> 1)) & 0x01010101u;              // 1 where p != I
-    return d ? (ne & nz) : 0u;
+    if (SPLIT) {
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+            if (ALL || ((vp >> (2 * n)) & 3u)) slots[n * a.n_pad + j] = out[n];
+    } else {
+        *reinterpret_cast<float4 *>(slots + 4 * j) = make_float4(out[0], out[1], out[2], out[3]);
+    }
 }
 
 // Per-thread adjacency of the owned checks and qubits of one code:
@@ -301,7 +345,6 @@ __device__ __forceinline__ void load_prior(const DecodeArgs &a, float *PiS) {
 // (base = the staged table): table | Pi [3][Np] | groups.
 struct GroupMem {
     float *PiS, *slots, *state;
-    uint8_t *abits;
 };
 
 __device__ __forceinline__ GroupMem group_mem(const DecodeArgs &a, uint8_t *base, int group) {
@@ -309,8 +352,7 @@ __device__ __forceinline__ GroupMem group_mem(const DecodeArgs &a, uint8_t *base
     m.PiS = reinterpret_cast<float *>(base + a.table_bytes);
     uint8_t *g = base + a.table_bytes + (size_t)12 * a.n_pad + (size_t)group * a.group_bytes;
     m.slots = reinterpret_cast<float *>(g);
-    m.abits = reinterpret_cast<uint8_t *>(m.slots + a.slots_floats);
-    m.state = reinterpret_cast<float *>(m.abits + ((a.slots_floats + 15u) & ~15u));
+    m.state = m.slots + a.slots_floats;
     return m;
 }
 
@@ -318,14 +360,13 @@ __device__ __forceinline__ GroupMem group_mem(const DecodeArgs &a, uint8_t *base
 // then iterations of the check pass and the variable pass until the hard
 // decision satisfies the syndrome or max_iter is reached; writes the shot's
 // outputs.  npt <= NPT is the number of nodes each thread owns.
-template <int VARIANT, int NPT, bool TRACE, bool NOY>
-__device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj<NPT> &adj, const GroupMem &m,
-                                            int npt, int T, int tg, int G, int bar_id, int shot) {
+template <int VARIANT, int NPT, bool TRACE, bool SPLIT>
+__device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<NPT> &adj, const GroupMem &m,
+                                           int npt, int T, int tg, int G, int bar_id, int shot, float alpha) {
     const int N = a.N, M = a.M, Np = a.n_pad;
     const uint32_t kZero = 4u * (uint32_t)Np, kTrash = kZero + 1u;
     float *slots = m.slots, *state = m.state;
     const float *PiS = m.PiS;
-    uint8_t *abits = m.abits;
 
     // syndrome bits of the owned checks (bit k <-> check k*T + tg)
     uint32_t sbits = 0;
@@ -358,7 +399,8 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj
                 state[5 * Np + j] = 0.f;
             }
             const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-            emit_v2c<TRACE, NOY>(a, slots, j, 0, shot, adj.info[k] >> 8, PX, PY, PZ, z4);
+            emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, true>(a, slots, j, 0, shot, adj.info[k] >> 8, PX, PY,
+                                                                  PZ, z4, 0u);
         }
     }
     group_sync(G, bar_id);
@@ -377,22 +419,39 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj
                 const uint32_t sl[4] = {adj.cs_lo[k] & 0xFFFFu, adj.cs_lo[k] >> 16, adj.cs_hi[k] & 0xFFFFu,
                                         adj.cs_hi[k] >> 16};
                 const uint32_t sb = (sbits >> k) & 1u;
-                if (do_check) mismatch |= sb ^ abits[sl[0]] ^ abits[sl[1]] ^ abits[sl[2]] ^ abits[sl[3]];
+                uint32_t u[4];
+#pragma unroll
+                for (int n = 0; n < 4; ++n) u[n] = __float_as_uint(slots[sl[n]]);
+                // bit 31: the product of the incoming signs; bit 0: the parity
+                // of the previous decision on this check's edges
+                const uint32_t ux = u[0] ^ u[1] ^ u[2] ^ u[3];
+                if (do_check) mismatch |= (ux ^ sb) & 1u;
                 if (do_msgs) {
-                    uint32_t u[4];
                     float mag[4];
 #pragma unroll
-                    for (int n = 0; n < 4; ++n) {
-                        u[n] = __float_as_uint(slots[sl[n]]);
-                        mag[n] = __uint_as_float(u[n] & 0x7FFFFFFFu);
-                    }
+                    for (int n = 0; n < 4; ++n) mag[n] = __uint_as_float(u[n] & 0x7FFFFFFEu);
                     // (-1)^{s_i} times the product of the incoming signs
-                    const uint32_t sgn = (u[0] ^ u[1] ^ u[2] ^ u[3] ^ (sb << 31)) & 0x80000000u;
-                    const float e01 = mag[0] + mag[1], e23 = mag[2] + mag[3];
-                    const float ext[4] = {mag[1] + e23, mag[0] + e23, e01 + mag[3], e01 + mag[2]};
+                    const uint32_t sgn = (ux ^ (sb << 31)) & 0x80000000u;
+                    float ext[4];
+                    if (PhiForm<VARIANT>::value) {
+                        // extrinsic sums of phi(|m|) over the other three edges
+                        const float e01 = mag[0] + mag[1], e23 = mag[2] + mag[3];
+                        ext[0] = mag[1] + e23;
+                        ext[1] = mag[0] + e23;
+                        ext[2] = e01 + mag[3];
+                        ext[3] = e01 + mag[2];
+                    } else {
+                        // extrinsic D of each edge: the (+) of the other three deltas
+                        const float d01 = oplus(mag[0], mag[1]), d23 = oplus(mag[2], mag[3]);
+                        ext[0] = oplus(mag[1], d23);
+                        ext[1] = oplus(mag[0], d23);
+                        ext[2] = oplus(d01, mag[3]);
+                        ext[3] = oplus(d01, mag[2]);
+                    }
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
-                        const float wv = fminf(phi_check(ext[n]), a.clip);
+                        const float wv = fminf(PhiForm<VARIANT>::value ? phi_check(ext[n]) : c2v_magnitude(ext[n]),
+                                               a.clip);
                         const float mm = __uint_as_float(__float_as_uint(wv) ^ ((sgn ^ u[n]) & 0x80000000u));
                         slots[sl[n] == kZero ? kTrash : sl[n]] = mm;
                         if (TRACE && a.tr_c2v && sl[n] != kZero)
@@ -418,11 +477,24 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj
         for (int k = 0; k < NPT; ++k) {
             const int j = k * T + tg;
             if (k < npt && j < N) {
-                const float4 w4 = *reinterpret_cast<const float4 *>(slots + 4 * j);
-                const float win[4] = {w4.x, w4.y, w4.z, w4.w};
                 const uint32_t vp = adj.info[k] >> 8;
-                float S[3];
-                anticommuting_sums<NOY>(vp, win, S[0], S[1], S[2]);
+                float win[4], S[3];
+                if (SPLIT) {
+                    // positions 0, 1: X-type edges (anticommute with Z and Y);
+                    // 2, 3: Z-type edges (with X and Y); unused slots hold 0
+#pragma unroll
+                    for (int n = 0; n < 4; ++n) win[n] = slots[n * Np + j];
+                    S[2] = win[0] + win[1];
+                    S[0] = win[2] + win[3];
+                    S[1] = S[0] + S[2];
+                } else {
+                    const float4 w4 = *reinterpret_cast<const float4 *>(slots + 4 * j);
+                    win[0] = w4.x;
+                    win[1] = w4.y;
+                    win[2] = w4.z;
+                    win[3] = w4.w;
+                    anticommuting_sums(vp, win, S[0], S[1], S[2]);
+                }
                 const float Pi[3] = {PiS[j], PiS[Np + j], PiS[2 * Np + j]};
                 float Q[3];
 #pragma unroll
@@ -432,7 +504,7 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj
                     } else if (VARIANT == BPQ_EWAINIT) {
                         // eq. (EWAInit): Pi^(t) = alpha Pi^(0) + (1-alpha) Q^(t-1), t > 1
                         const float qp = state[w * Np + j];
-                        const float pit = t > 1 ? a.alpha * Pi[w] + (1.f - a.alpha) * qp : Pi[w];
+                        const float pit = t > 1 ? alpha * Pi[w] + (1.f - alpha) * qp : Pi[w];
                         Q[w] = pit + S[w];
                         state[w * Np + j] = Q[w];
                     } else if (VARIANT == BPQ_MOMENTUM) {
@@ -465,8 +537,9 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj
                     if (Q[2] < mq) d = 3;
                 }
                 dk[k] = d;
-                // per-edge <E^_j, H_ij> for the next syndrome test
-                reinterpret_cast<uint32_t *>(abits)[j] = anti_bytes(d, adj.pp[k]);
+                // per-edge <E^_j, H_ij> for the next syndrome test (carried in the
+                // messages' least significant bits)
+                const uint32_t ab = SPLIT ? anti_bytes_split(d) : anti_bytes(d, adj.pp[k]);
                 if (TRACE) {
                     const size_t o = (size_t)shot * a.max_iter + (t - 1);
                     if (a.tr_Q) {
@@ -476,7 +549,8 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj
                     }
                     if (a.tr_dec) a.tr_dec[o * N + j] = (uint8_t)d;
                 }
-                emit_v2c<TRACE, NOY>(a, slots, j, t, shot, vp, Q[0], Q[1], Q[2], win);
+                emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, false>(a, slots, j, t, shot, vp, Q[0], Q[1], Q[2],
+                                                                       win, ab);
             }
         }
         group_sync(G, bar_id);
@@ -494,11 +568,12 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs &a, const ThreadAdj
         a.conv[shot] = (uint8_t)conv;
         a.iters[shot] = (uint8_t)iters;
     }
+    return conv;
 }
 
 // One code per launch: a persistent grid; every shot group takes shots from
 // the global queue until the batch is exhausted.
-template <int VARIANT, int NPT, bool TRACE, bool NOY>
+template <int VARIANT, int NPT, bool TRACE, bool SPLIT>
 __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
@@ -524,10 +599,7 @@ __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const 
         bulk_g2s(tab, a.table, a.table_bytes, mbar);
     }
     load_prior(a, m.PiS);
-    if (tg == 0) {
-        m.slots[4 * a.n_pad] = 0.f;  // the zero slot
-        m.abits[4 * a.n_pad] = 0;
-    }
+    if (tg == 0) m.slots[4 * a.n_pad] = 0.f;  // the zero slot
     const bool staged = mbar_wait_bounded(mbar, 0, 1u << 22);
     if (__syncthreads_or(!staged)) {
         if (tid == 0) atomicExch(a.work + 1, 1u);
@@ -543,7 +615,16 @@ __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const 
         group_sync(G, bar_id);
         const int shot = grp_shot[group];
         if (shot >= a.B) break;
-        decode_shot<VARIANT, NPT, TRACE, NOY>(a, adj, m, NPT, T, tg, G, bar_id, shot);
+        if (VARIANT == BPQ_AEWA) {
+            // Appendix C: EWAInit-BP with alpha = 1.0, 0.9, ..., 0.0 in turn until
+            // a run converges (the outputs are those of the last run)
+            for (int k = 0; k <= 10; ++k)
+                if (decode_shot<BPQ_EWAINIT, NPT, TRACE, SPLIT>(a, adj, m, NPT, T, tg, G, bar_id, shot,
+                                                              1.0f - 0.1f * (float)k))
+                    break;
+        } else {
+            decode_shot<VARIANT, NPT, TRACE, SPLIT>(a, adj, m, NPT, T, tg, G, bar_id, shot, a.alpha);
+        }
     }
 }
 
@@ -602,7 +683,6 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
             if (group < desc->groups_per_cta && tid - group * T == 0) {
                 const GroupMem m = group_mem(*desc, tab, group);
                 m.slots[4 * desc->n_pad] = 0.f;
-                m.abits[4 * desc->n_pad] = 0;
             }
             load_adjacency<NPT>(*desc, tab, T, tid - group * T, desc->npt, adj);
             __syncthreads();
@@ -619,10 +699,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
                 group_sync(G, bar_id);
                 const int k = grp_shot[group];
                 if (k >= td.z) break;
-                if (a.noy)
-                    decode_shot<VARIANT, NPT, false, true>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k);
+                if (a.split)
+                    decode_shot<VARIANT, NPT, false, true>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k, a.alpha);
                 else
-                    decode_shot<VARIANT, NPT, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k);
+                    decode_shot<VARIANT, NPT, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k, a.alpha);
             }
         }
         __syncthreads();
@@ -632,12 +712,30 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
 
 }  // namespace dk
 
+// AEWA-BP: single-code, non-trace kernels only.
+#define BPQ_DEFINE_PICK_AEWA(NAME)                                                       \
+    DecodeKernelFn NAME(int npt, bool trace, bool split) {                                 \
+        if (trace) return nullptr;                                                       \
+        switch (npt) {                                                                   \
+            case 1: return split ? dk::decode_kernel<BPQ_AEWA, 1, false, true>             \
+                               : dk::decode_kernel<BPQ_AEWA, 1, false, false>;           \
+            case 2: return split ? dk::decode_kernel<BPQ_AEWA, 2, false, true>             \
+                               : dk::decode_kernel<BPQ_AEWA, 2, false, false>;           \
+            case 3: return split ? dk::decode_kernel<BPQ_AEWA, 3, false, true>             \
+                               : dk::decode_kernel<BPQ_AEWA, 3, false, false>;           \
+            case 4: return split ? dk::decode_kernel<BPQ_AEWA, 4, false, true>             \
+                               : dk::decode_kernel<BPQ_AEWA, 4, false, false>;           \
+        }                                                                                \
+        return nullptr;                                                                  \
+    }                                                                                    \
+    BatchKernelFn NAME##_batch(int) { return nullptr; }
+
 // Instantiate the kernels of one variant and return the one for (NPT,
-// trace, no-Y code).
+// trace, split layout).
 #define BPQ_PICK_NPT(V, NPT, TR)                                                         \
-    (noy ? dk::decode_kernel<V, NPT, TR, true> : dk::decode_kernel<V, NPT, TR, false>)
+    (split ? dk::decode_kernel<V, NPT, TR, true> : dk::decode_kernel<V, NPT, TR, false>)
 #define BPQ_DEFINE_PICK(NAME, V)                                                         \
-    DecodeKernelFn NAME(int npt, bool trace, bool noy) {                                 \
+    DecodeKernelFn NAME(int npt, bool trace, bool split) {                                 \
         switch (npt * 2 + (trace ? 1 : 0)) {                                             \
             case 2: return BPQ_PICK_NPT(V, 1, false);                                    \
             case 3: return BPQ_PICK_NPT(V, 1, true);                                     \

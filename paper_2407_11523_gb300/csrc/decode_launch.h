@@ -26,10 +26,11 @@ struct DecodeArgs {
     int G;                     // warps per shot group
     int n_pad;                 // N rounded up to a multiple of 4 (shared-memory array stride)
     uint32_t slots_floats, group_bytes;
-    float alpha, gamma, eps, clip, phi_clip;
+    float alpha, gamma, eps, clip, delta_clip, phi_clip;
     int ada_from1;
+    int split;                 // table in the split layout (bpq_tanner::split)
     // used by the batched kernel only
-    int npt, groups_per_cta, noy;
+    int npt, groups_per_cta;
 };
 
 constexpr uint32_t kDescBytes = (sizeof(DecodeArgs) + 15) & ~15u;  // descriptor copy in shared memory
@@ -54,15 +55,17 @@ struct LaunchShape {
 using DecodeKernelFn = void (*)(const DecodeArgs);
 using BatchKernelFn = void (*)(const BatchArgs);
 
-// Kernels of one variant, for nodes per thread npt in [1, 4]; noy selects the
-// specialisation for codes without Y entries.
-DecodeKernelFn pick_plain(int npt, bool trace, bool noy);
+// Kernels of one variant, for nodes per thread npt in [1, 4]; split selects the
+// specialisation for tables in the split layout.
+DecodeKernelFn pick_plain(int npt, bool trace, bool split);
 BatchKernelFn pick_plain_batch(int npt);
-DecodeKernelFn pick_momentum(int npt, bool trace, bool noy);
+DecodeKernelFn pick_momentum(int npt, bool trace, bool split);
 BatchKernelFn pick_momentum_batch(int npt);
-DecodeKernelFn pick_adagrad(int npt, bool trace, bool noy);
+DecodeKernelFn pick_adagrad(int npt, bool trace, bool split);
 BatchKernelFn pick_adagrad_batch(int npt);
-DecodeKernelFn pick_ewainit(int npt, bool trace, bool noy);
+DecodeKernelFn pick_ewainit(int npt, bool trace, bool split);
+DecodeKernelFn pick_aewa(int npt, bool trace, bool split);
+BatchKernelFn pick_aewa_batch(int npt);
 BatchKernelFn pick_ewainit_batch(int npt);
 
 int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s);

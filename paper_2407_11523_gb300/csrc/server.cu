@@ -64,6 +64,7 @@ struct bpq_server {
     bpq::BatchKernelFn fn = nullptr;
     size_t smem = 0;
     int ctas = 0;
+    long launches = 0;  // batched kernel launches since creation
     std::vector<Lane> lanes;
 };
 
@@ -150,9 +151,6 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
         a.group_bytes = sh.group_bytes;
         a.npt = sh.npt;
         a.groups_per_cta = gpc;
-        bool noy = true;
-        for (uint8_t p : t->chk_pauli) noy = noy && p != 2;
-        a.noy = noy ? 1 : 0;
         npt_max = std::max(npt_max, sh.npt);
         s->smem = std::max(s->smem, sh.smem);
         s->codes.push_back(t);
@@ -319,6 +317,7 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
             if (e == cudaSuccess) {
                 s->fn<<<(unsigned)std::min(s->ctas, ntiles), bpq::kBatchThreads, s->smem, L.st>>>(args);
                 e = cudaGetLastError();
+                ++s->launches;
             }
             if (e == cudaSuccess) e = cudaMemcpyAsync(L.est_h, L.est, nsum, cudaMemcpyDeviceToHost, L.st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(L.conv_h, L.conv, shot, cudaMemcpyDeviceToHost, L.st);
@@ -332,6 +331,12 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
         max_busy = std::max(max_busy, busy);
     }
     if (lanes_used) *lanes_used = max_busy;
+    return BPQ_OK;
+}
+
+int bpq_server_stats(const bpq_server *s, long *launches) {
+    if (!s) return fail(BPQ_EINVAL, "server is NULL");
+    if (launches) *launches = s->launches;
     return BPQ_OK;
 }
 

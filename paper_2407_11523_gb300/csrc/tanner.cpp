@@ -76,14 +76,19 @@ int build_tables(bpq_tanner *t) {
     for (int k = 0; k < M_pad * 4; ++k) slot[k] = kNoSlot;
     t->var_canon.assign((size_t)4 * N, -1);
 
+    // Qubit j's edges occupy slots 4j .. 4j+3, its k-th edge at position
+    // (k + (j >> 3)) mod 4.  The rotation spreads the check pass's accesses
+    // (32 consecutive checks touch about 32 consecutive qubits) over all 32
+    // shared-memory banks instead of the 8 that slot 4j + k would hit.
     std::vector<int> slot_of_edge(t->E, -1);
     for (int j = 0; j < N; ++j) {
         uint8_t bits = 0;
         for (size_t k = 0; k < var_edges[j].size(); ++k) {
-            int e = var_edges[j][k];
-            slot_of_edge[e] = 4 * j + (int)k;
-            t->var_canon[4 * j + k] = e;
-            bits |= (uint8_t)(t->chk_pauli[e] << (2 * k));
+            const int e = var_edges[j][k];
+            const int pos = ((int)k + (j >> 3)) & 3;
+            slot_of_edge[e] = 4 * j + pos;
+            t->var_canon[4 * j + pos] = e;
+            bits |= (uint8_t)(t->chk_pauli[e] << (2 * pos));
         }
         vp[j] = bits;
     }
@@ -94,6 +99,46 @@ int build_tables(bpq_tanner *t) {
             bits |= (uint8_t)(t->chk_pauli[e] << (2 * n));
         }
         cp[i] = bits;
+    }
+
+    // split layout (see bpq_tanner::split)
+    t->split = true;
+    for (int j = 0; j < N && t->split; ++j) {
+        int nx = 0, nz = 0;
+        for (int e : var_edges[j]) {
+            const uint8_t p = t->chk_pauli[e];
+            nx += p == 1;
+            nz += p == 3;
+            if (p == 2) t->split = false;
+        }
+        if (nx > 2 || nz > 2) t->split = false;
+    }
+    t->table_split.clear();
+    t->var_canon_split.clear();
+    if (t->split) {
+        const int n4 = (N + 3) & ~3;
+        t->table_split.assign(t->table.size(), 0);
+        t->var_canon_split.assign((size_t)4 * n4, -1);
+        uint16_t *slot2 = reinterpret_cast<uint16_t *>(t->table_split.data());
+        uint8_t *cp2 = t->table_split.data() + t->off_chk_pauli;
+        uint8_t *vp2 = t->table_split.data() + t->off_var_pauli;
+        for (int k = 0; k < M_pad * 4; ++k) slot2[k] = kNoSlot;
+        for (int j = 0; j < N; ++j) {
+            int nx = 0, nz = 0;
+            uint8_t bits = 0;
+            for (int e : var_edges[j]) {
+                const uint8_t p = t->chk_pauli[e];
+                const int pos = p == 1 ? nx++ : 2 + nz++;
+                slot_of_edge[e] = pos * n4 + j;
+                t->var_canon_split[(size_t)pos * n4 + j] = e;
+                bits |= (uint8_t)(p << (2 * pos));
+            }
+            vp2[j] = bits;
+        }
+        for (int i = 0; i < M; ++i)
+            for (int e = t->chk_ptr[i], n = 0; e < t->chk_ptr[i + 1]; ++e, ++n)
+                slot2[4 * i + n] = (uint16_t)slot_of_edge[e];
+        std::memcpy(cp2, cp, (size_t)M_pad);
     }
     return BPQ_OK;
 }
@@ -164,7 +209,7 @@ extern "C" {
 
 void bpq_default_params(int variant, bpq_params *out) {
     if (!out) return;
-    out->alpha = variant == BPQ_ADAGRAD ? 5.0f : variant == BPQ_PLAIN ? 1.0f : 0.5f;
+    out->alpha = variant == BPQ_ADAGRAD ? 5.0f : (variant == BPQ_PLAIN || variant == BPQ_AEWA) ? 1.0f : 0.5f;
     out->gamma = 0.0f;
     out->eps = 1e-8f;
     out->msg_clip = 30.0f;

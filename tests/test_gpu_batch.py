@@ -98,3 +98,37 @@ def test_batched_results_match_oracle_sample(bpq):
         total += B
     assert stable_total >= 0.9 * total
     assert agree >= 0.999 * stable_total, (agree, stable_total)
+
+
+def y_rotated(H, qubits):
+    """The code with X and Y exchanged on the given qubits (a single-qubit
+    Clifford): still a stabilizer code, now with Y entries, so it takes the
+    decoder's generic table layout instead of the split one."""
+    H = H.copy()
+    for j in qubits:
+        col = H[:, j].copy()
+        H[col == 1, j] = 2
+        H[col == 2, j] = 1
+    return H
+
+
+@pytest.mark.parametrize("variant", ["ewainit", "adagrad"])
+def test_batched_mixed_layouts(bpq, variant):
+    """Codes in the generic layout (Y entries) and in the split layout share
+    one batched launch; each result equals the one-code decoder's."""
+    from inputs import random_tree_code
+    rng = np.random.default_rng(5)
+    H7 = bpq.Tanner("planar", 7).dense()
+    codes = [bpq.Tanner(H=random_tree_code(8, seed=3)), bpq.Tanner("planar", 7),
+             bpq.Tanner(H=y_rotated(H7, rng.choice(H7.shape[1], 30, replace=False))), bpq.Tanner("toric", 6)]
+    ch = oracle.depolarizing(0.06)
+    items = []
+    for k, t in enumerate(codes):
+        _, syn = bpq.sample(t, *ch, seed=400 + k, shot0=0, B=700 + 37 * k)
+        items.append((t, syn, bpq.prior_tensor(t, *ch)))
+    plan = bpq.BatchPlan(items, variant=variant, max_iter=60, tile_shots=16)
+    outs = plan.run()
+    for (t, syn, prior), got in zip(items, outs):
+        ref = bpq.decode(t, syn, prior, variant, max_iter=60)
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b), (t.N, variant)

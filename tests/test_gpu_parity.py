@@ -144,6 +144,24 @@ def test_messages_trees_and_trapping_set(bpq, variant):
     checked_trace(rec, H, s, prior, variant, 5, [0], min_checked_frac=0.0)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_messages_code_with_y_entries(bpq, variant):
+    """A planar d = 7 code with X and Y exchanged on 30 qubits (a valid
+    stabilizer code with Y entries): the decoder's generic table layout."""
+    H7 = bpq.Tanner("planar", 7).dense()
+    H = H7.copy()
+    for j in np.random.default_rng(5).choice(H.shape[1], 30, replace=False):
+        col = H7[:, j]
+        H[col == 1, j] = 2
+        H[col == 2, j] = 1
+    t = bpq.Tanner(H=H)
+    _, s = oracle.sample(H, *oracle.depolarizing(0.06), seed=23, shot0=0, B=60)
+    prior = random_priors(t.N, seed=9, lo=0.01, hi=0.08)
+    syn, pri = gpu_inputs(bpq, t, s, prior)
+    rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5).items()}
+    checked_trace(rec, H, s, prior, variant, 5, range(60), min_checked_frac=0.5)
+
+
 def ler_interval(fails):
     n = fails.size
     p = fails.mean()
@@ -325,3 +343,62 @@ def test_full_size_toric_d15_bench_configuration(bpq, p, min_stable):
     # their 100-iteration trajectories are chaotic (unstable in the oracle too)
     assert stable.mean() >= min_stable
     assert same[stable].mean() >= 0.999, (same[stable].mean(), stable.mean())
+
+
+@pytest.mark.parametrize("L", [3, 7, 11])
+def test_aewa_planar_matches_oracle(bpq, L):
+    """AEWA-BP (Appendix C) on its planar workloads, depolarising p = 0.06:
+    decisions on the oracle-stable shots (8-ulp prior perturbation), the
+    convergence flag and the logical error rate against the FP64 oracle; the
+    iteration count is that of the last EWAInit-BP run."""
+    t = bpq.Tanner("planar", L)
+    H = t.dense()
+    ch = oracle.depolarizing(0.06)
+    B = 4000
+    err_g, syn_g = bpq.sample(t, *ch, seed=0xAE3A0000 + L, shot0=0, B=B)
+    est, conv, iters = bpq.decode(t, syn_g, bpq.prior_tensor(t, *ch), variant="aewa", max_iter=60)
+    fail_g = bpq.check_logical(t, err_g, est)
+    torch.cuda.synchronize()
+    est, conv, iters, fail_g = (x.cpu().numpy() for x in (est, conv, iters, fail_g))
+
+    e_ref, s_ref = oracle.sample(H, *ch, seed=0xAE3A0000 + L, shot0=0, B=B)
+    prior = f32(np.tile(ch, (t.N, 1)))
+    est_r, conv_r, iters_r = oracle.decode(H, s_ref, prior, variant="aewa", max_iter=60, nthreads=NTHREADS)
+    rng = np.random.default_rng(13)
+    stable = np.ones(B, dtype=bool)
+    for _ in range(3):
+        pp = prior * (1 + 2.0 ** -20 * rng.choice([-1.0, 1.0], size=prior.shape))
+        stable &= (oracle.decode(H, s_ref, pp, "aewa", max_iter=60, nthreads=NTHREADS)[0] == est_r).all(axis=1)
+    same = (est == est_r).all(axis=1)
+    assert stable.mean() >= 0.97, stable.mean()
+    # A shot that no alpha converges returns the last iterate of the alpha = 0
+    # run, where Pi^(t) = Q^(t-1) (eq. (EWAInit)) accumulates every S without
+    # the prior's anchor: |Q| grows with t and the fp32 trajectory leaves the
+    # FP64 one.  Such a shot is a declared failure (converged = 0) on both
+    # sides, so its estimate is not compared.
+    cmp = stable & conv_r
+    assert same[cmp].mean() >= 0.999, (same[cmp].mean(), same.mean())
+    assert (conv.astype(bool) == conv_r).mean() >= 0.995
+    fail_r, _ = codes.logical_failure(H, e_ref, est_r)
+    pg, sg = ler_interval(fail_g > 0)
+    pr, sr = ler_interval(fail_r)
+    assert abs(pg - pr) <= max(sg, sr), (pg, pr)
+    assert ((iters >= 0) & (iters <= 60)).all() and (iters[conv == 0] == 60).all()
+    assert (fail_g[conv == 1] != 1).all() and (fail_g[conv == 0] == 1).all()
+
+
+def test_aewa_host_path_and_refusals(bpq):
+    """AEWA-BP through the host-buffer entry point equals the device one; the
+    trace and batched entry points refuse it with an error, not a launch."""
+    t = bpq.Tanner("planar", 7)
+    ch = oracle.depolarizing(0.08)
+    _, syn = bpq.sample(t, *ch, seed=5, shot0=0, B=1500)
+    prior = bpq.prior_tensor(t, *ch)
+    dev = bpq.decode(t, syn, prior, "aewa", max_iter=60)
+    host = bpq.decode_host(t, syn.cpu().pin_memory(), prior.cpu().pin_memory(), "aewa", max_iter=60)
+    for a, b in zip(dev, host):
+        assert torch.equal(a.cpu(), b)
+    with pytest.raises(bpq.BPQError):
+        bpq.decode_trace(t, syn[:4].contiguous(), prior, "aewa", T=5)
+    with pytest.raises(bpq.BPQError):
+        bpq.BatchPlan([(t, syn, prior)], "aewa", max_iter=60)

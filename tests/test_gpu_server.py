@@ -43,6 +43,8 @@ def test_server_results_equal_alone(bpq, rate, lanes, max_batch):
     code_of, arrival, syn_list = make_trace(bpq, codes, R, rate, seed=21)
     ests, conv, iters, done, used = srv.replay(code_of, arrival, syn_list)
     assert (done >= arrival).all() and used >= 1
+    # every dispatch is one batched launch, of at most max_batch requests
+    assert -(-R // max_batch) <= srv.launches() <= R
     # each request alone: a launch of one shot per request for a sample, and
     # the per-code batch (shot results are independent of the batch) for all
     for c, t in enumerate(codes):
