@@ -59,9 +59,9 @@ def lib():
         L = ctypes.CDLL(_SO)
         P = ctypes.c_void_p
         i, d, u64 = ctypes.c_int, ctypes.c_double, ctypes.c_uint64
-        L.oracle_decode.argtypes = [i, i, P, i, P, P, i, d, d, d, d, i, i, P, P, P, i]
+        L.oracle_decode.argtypes = [i, i, P, i, P, P, i, d, d, d, d, i, i, i, P, P, P, i]
         L.oracle_decode.restype = i
-        L.oracle_trace.argtypes = [i, i, P, P, P, i, d, d, d, d, i, i, P, P, P, P, P, P]
+        L.oracle_trace.argtypes = [i, i, P, P, P, i, d, d, d, d, i, i, i, P, P, P, P, P, P]
         L.oracle_trace.restype = i
         L.oracle_sample.argtypes = [i, i, P, d, d, d, u64, u64, i, P, P]
         L.oracle_sample.restype = i
@@ -109,10 +109,15 @@ def _params(variant, alpha, gamma, eps, msg_clip, adagrad_g_from_iter1):
             1 if adagrad_g_from_iter1 is None else int(adagrad_g_from_iter1))
 
 
+SCHEDULES = {"parallel": 0, "serial": 1}
+
+
 def decode(H, syn, prior, variant=PLAIN, max_iter=50, alpha=None, gamma=None, eps=None,
-           msg_clip=None, adagrad_g_from_iter1=None, nthreads=1):
+           msg_clip=None, adagrad_g_from_iter1=None, nthreads=1, schedule="parallel"):
     """Decode B syndromes. syn: (B, M) 0/1; prior: (N, 3) probabilities
-    (p^X, p^Y, p^Z).  Returns (est (B,N) codes, conv (B,) bool, iters (B,))."""
+    (p^X, p^Y, p^Z).  schedule: "parallel" (flooding) or "serial"
+    (Algorithm 1's qubit-by-qubit sweep).  Returns (est (B,N) codes,
+    conv (B,) bool, iters (B,))."""
     H = np.ascontiguousarray(H, dtype=np.uint8)
     M, N = H.shape
     syn = np.ascontiguousarray(np.atleast_2d(syn), dtype=np.uint8).reshape(-1, M)
@@ -124,14 +129,14 @@ def decode(H, syn, prior, variant=PLAIN, max_iter=50, alpha=None, gamma=None, ep
     iters = np.zeros(B, dtype=np.int32)
     a, g, e, c, f = _params(variant, alpha, gamma, eps, msg_clip, adagrad_g_from_iter1)
     rc = lib().oracle_decode(N, M, _ptr(H), B, _ptr(syn), _ptr(prior), variant, a, g, e, c, f,
-                             max_iter, _ptr(est), _ptr(conv), _ptr(iters), nthreads)
+                             SCHEDULES[schedule], max_iter, _ptr(est), _ptr(conv), _ptr(iters), nthreads)
     if rc:
         raise ValueError(f"oracle_decode failed ({rc})")
     return est, conv.astype(bool), iters
 
 
 def trace(H, syn, prior, variant=PLAIN, T=5, alpha=None, gamma=None, eps=None, msg_clip=None,
-          adagrad_g_from_iter1=None):
+          adagrad_g_from_iter1=None, schedule="parallel"):
     """Run exactly T iterations on one syndrome and return every intermediate
     quantity: dict with m_v2c (T+1, E), m_c2v (T, E), S, Q, aux (T, N, 3) and
     dec (T, N).  Edges are in check-major order (row i of H, columns j
@@ -145,7 +150,8 @@ def trace(H, syn, prior, variant=PLAIN, T=5, alpha=None, gamma=None, eps=None, m
     out = dict(m_v2c=np.zeros((T + 1, E)), m_c2v=np.zeros((T, E)), S=np.zeros((T, N, 3)),
                Q=np.zeros((T, N, 3)), aux=np.zeros((T, N, 3)), dec=np.zeros((T, N), dtype=np.uint8))
     a, g, e, c, f = _params(variant, alpha, gamma, eps, msg_clip, adagrad_g_from_iter1)
-    rc = lib().oracle_trace(N, M, _ptr(H), _ptr(syn), _ptr(prior), variant, a, g, e, c, f, T,
+    rc = lib().oracle_trace(N, M, _ptr(H), _ptr(syn), _ptr(prior), variant, a, g, e, c, f,
+                            SCHEDULES[schedule], T,
                             _ptr(out["m_v2c"]), _ptr(out["m_c2v"]), _ptr(out["S"]), _ptr(out["Q"]),
                             _ptr(out["aux"]), _ptr(out["dec"]))
     if rc:

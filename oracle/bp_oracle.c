@@ -138,6 +138,7 @@ static void graph_free(graph *g) {
 typedef struct {
     double alpha, gamma, eps, msg_clip;
     int adagrad_g_from_iter1;
+    int serial;  /* 0: parallel (flooding) schedule; 1: serial schedule of Algorithm 1 */
 } params;
 
 /* Optional per-iteration record of one shot (all arrays may be NULL). */
@@ -197,6 +198,90 @@ static int syndrome_matches(const graph *g, const uint8_t *est, const uint8_t *s
     return 1;
 }
 
+/* m_{c_i -> v_j} of edge e (check i) from the current v->c messages of the
+ * other edges of check i, eq. (h_update) with the syndrome sign, clipped. */
+static double c2v_edge(const graph *g, const workspace *w, const uint8_t *syn, int e, double c) {
+    const int i = g->edge_chk[e];
+    long double prod = 1.0L;
+    for (int f = g->chk_ptr[i]; f < g->chk_ptr[i + 1]; ++f)
+        if (f != e) prod *= tanhl((long double)w->m_v2c[f] / 2.0L);
+    long double wv = 2.0L * atanhl(prod);
+    double m = (syn[i] & 1) ? -(double)wv : (double)wv;
+    return clip(m, c);
+}
+
+/* Posterior of one qubit-Pauli pair k = 3j + W for each variant, from the
+ * sum S of its anticommuting c->v messages (the rules of Sec. II-B1 and
+ * Sec. III, identical under both schedules). */
+static int posterior(int variant, const params *pr, int t, workspace *w, int k, double S) {
+    double Pi = w->Pi0[k], Qp = w->Qprev[k];
+    switch (variant) {
+    case OR_PLAIN: w->Q[k] = Pi + S; return 0;
+    case OR_EWAINIT: w->Q[k] = w->Pit[k] + S; return 0;
+    case OR_MOMENTUM: {
+        double grad = Qp - Pi - S;
+        w->gstate[k] = pr->gamma * w->gstate[k] + (1.0 - pr->gamma) * grad;
+        w->Q[k] = Qp - pr->alpha * w->gstate[k];
+        return 0;
+    }
+    case OR_ADAGRAD: {
+        double gp = Qp - Pi - S;
+        if (t >= 2 || pr->adagrad_g_from_iter1) w->gstate[k] += gp * gp;
+        w->Q[k] = t == 1 ? Pi + S : Qp - pr->alpha * gp / (sqrt(w->gstate[k]) + pr->eps);
+        return 0;
+    }
+    }
+    return -1;
+}
+
+/* One iteration of the serial schedule (Algorithm 1's serial update): the
+ * qubits are visited in order j = 1..N; at its turn qubit j takes the c->v
+ * messages of its checks from the v->c messages as they stand (already
+ * updated in this iteration for the qubits before j), updates its
+ * posterior (EWAInit: with Pi^(t)_j = alpha Pi^(0)_j + (1 - alpha) Q^(t-1)_j
+ * for t > 1), and sends its new v->c messages: eq. (v_update) for plain and
+ * EWAInit BP, eq. (mombp5) for Momentum and AdaGrad BP. */
+static int serial_sweep(const graph *g, const uint8_t *syn, int variant, const params *pr, int t, workspace *w) {
+    const double c = pr->msg_clip;
+    for (int j = 0; j < g->N; ++j) {
+        if (variant == OR_EWAINIT && t > 1)
+            for (int k = 0; k < 3; ++k)
+                w->Pit[3 * j + k] = pr->alpha * w->Pi0[3 * j + k] + (1.0 - pr->alpha) * w->Qprev[3 * j + k];
+        for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
+            const int e = g->var_edges[a];
+            w->m_c2v[e] = c2v_edge(g, w, syn, e, c);
+        }
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
+                const int e = g->var_edges[a];
+                if (anticommutes(k + 1, g->edge_p[e])) s += w->m_c2v[e];
+            }
+            w->S[3 * j + k] = s;
+            if (posterior(variant, pr, t, w, 3 * j + k, s)) return -1;
+        }
+        for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
+            const int e = g->var_edges[a], h = g->edge_p[e];
+            double q[3];
+            for (int k = 0; k < 3; ++k) {
+                if (variant == OR_PLAIN || variant == OR_EWAINIT) {
+                    const double *base = (variant == OR_EWAINIT) ? &w->Pit[3 * j] : &w->Pi0[3 * j];
+                    double s = 0.0;
+                    for (int b = g->var_ptr[j]; b < g->var_ptr[j + 1]; ++b) {
+                        const int f = g->var_edges[b];
+                        if (f != e && anticommutes(k + 1, g->edge_p[f])) s += w->m_c2v[f];
+                    }
+                    q[k] = base[k] + s;
+                } else {
+                    q[k] = w->Q[3 * j + k] - (anticommutes(k + 1, h) ? w->m_c2v[e] : 0.0);
+                }
+            }
+            w->m_v2c[e] = clip(lambda_fn(h, q), c);
+        }
+    }
+    return 0;
+}
+
 /* Decode one shot.  stop_early = 1 applies the stopping rule; 0 runs exactly
  * max_iter iterations (used for recording traces).  Returns the number of
  * iterations run; *converged reports whether the last decision matched. */
@@ -225,6 +310,10 @@ static int decode_shot(const graph *g, const uint8_t *syn, const double *prior, 
 
     int t = 0, conv = 0;
     for (t = 1; t <= max_iter; ++t) {
+        if (pr->serial) {
+            if (serial_sweep(g, syn, variant, pr, t, w)) return -1;
+            goto decide;
+        }
         /* EWAInit-BP: Pi^(t) = alpha Pi^(0) + (1 - alpha) Q^(t-1) when t > 1, eq. (EWAInit). */
         if (variant == OR_EWAINIT && t > 1)
             for (int k = 0; k < 3 * N; ++k)
@@ -306,6 +395,7 @@ static int decode_shot(const graph *g, const uint8_t *syn, const double *prior, 
             w->m_v2c[e] = clip(lambda_fn(h, q), c);
         }
 
+    decide:
         /* Hard decision and stopping test. */
         for (int j = 0; j < N; ++j) w->est[j] = (uint8_t)hard_decision(&w->Q[3 * j]);
         conv = syndrome_matches(g, w->est, syn);
@@ -387,12 +477,13 @@ static void *run_job(void *arg) {
  * iters: B iteration counts.  nthreads > 1 splits the shots over threads. */
 int oracle_decode(int N, int M, const uint8_t *H, int B, const uint8_t *syn, const double *prior,
                   int variant, double alpha, double gamma, double eps, double msg_clip,
-                  int adagrad_g_from_iter1, int max_iter, uint8_t *est, uint8_t *conv,
+                  int adagrad_g_from_iter1, int serial, int max_iter, uint8_t *est, uint8_t *conv,
                   int32_t *iters, int nthreads) {
     if (N <= 0 || M < 0 || B < 0 || max_iter < 1 || variant < 0 || variant > 4) return -1;
+    if (serial && variant == OR_AEWA) return -1;
     graph g;
     if (graph_build(&g, N, M, H)) { graph_free(&g); return -2; }
-    params pr = {alpha, gamma, eps, msg_clip, adagrad_g_from_iter1};
+    params pr = {alpha, gamma, eps, msg_clip, adagrad_g_from_iter1, serial ? 1 : 0};
     if (nthreads < 1) nthreads = 1;
     if (nthreads > B) nthreads = B > 0 ? B : 1;
     job *jobs = calloc(nthreads, sizeof(job));
@@ -420,12 +511,12 @@ int oracle_decode(int N, int M, const uint8_t *H, int B, const uint8_t *syn, con
  * intermediate quantity in the caller's arrays (see struct trace). */
 int oracle_trace(int N, int M, const uint8_t *H, const uint8_t *syn, const double *prior,
                  int variant, double alpha, double gamma, double eps, double msg_clip,
-                 int adagrad_g_from_iter1, int T, double *m_v2c, double *m_c2v, double *S,
+                 int adagrad_g_from_iter1, int serial, int T, double *m_v2c, double *m_c2v, double *S,
                  double *Q, double *aux, uint8_t *dec) {
     if (N <= 0 || M < 0 || T < 1 || variant < 0 || variant > 3) return -1;
     graph g;
     if (graph_build(&g, N, M, H)) { graph_free(&g); return -2; }
-    params pr = {alpha, gamma, eps, msg_clip, adagrad_g_from_iter1};
+    params pr = {alpha, gamma, eps, msg_clip, adagrad_g_from_iter1, serial ? 1 : 0};
     workspace w;
     if (ws_alloc(&w, N, g.E)) { ws_free(&w); graph_free(&g); return -3; }
     trace tr = {m_v2c, m_c2v, S, Q, aux, dec};
