@@ -17,6 +17,18 @@ conclusion points to neural BP as a way to strengthen the algorithm):
         m_c->v^(t) = w_e (-1)^{s_i} 2 atanh(prod tanh(m_v->c^(t-1)/2))  (eq. (h_update)).
 
 With alpha_t = alpha, beta_t = 0 and w_e = 1 it is EWAInit-BP exactly.
+
+The Momentum model replaces the EWA prior by Momentum-BP's posterior
+recursion (Sec. III-A1, eqs. (mombp1), (mombp2) with the gradient of
+(mombp3)), with a trainable step alpha_t and momentum rate gamma_t:
+
+  g^(t) = gamma_t g^(t-1) + (1 - gamma_t) (Q^(t-1) - Pi^(0) - S^(t)),
+  Q^(t) = Q^(t-1) - alpha_t g^(t),         Q^(0) = Pi^(0), g^(0) = 0,
+
+and the same beta_t, w_e; alpha_t = alpha, gamma_t = gamma, beta_t = 0,
+w_e = 1 is Momentum-BP.  In both models the v->c message is lambda of the
+posterior minus the edge's own message (eq. (mombp5); for EWAInit this is
+eq. (v_update), since Q = Pi^(t) + S).
 Messages are clipped to [-clip, clip] as in the decoder.  The loss is the
 cross-entropy of the final posterior against the true error, averaged over
 qubits and shots: per qubit the log-probabilities of (I, X, Y, Z) are
@@ -70,9 +82,11 @@ def phi(x: torch.Tensor) -> torch.Tensor:
     return torch.log1p(2.0 / torch.expm1(x))
 
 
-def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0):
+def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0, model: str = "ewainit",
+            gamma=None):
     """Q^(T) (B, N, 3) of the unrolled decoder.  syn: (B, M) 0/1; prior:
-    (N, 3) probabilities; alpha, beta: (T,); w: (E,)."""
+    (N, 3) probabilities; alpha, beta (and gamma for model "momentum"):
+    (T,); w: (E,)."""
     syn = torch.as_tensor(np.asarray(syn), dtype=torch.float64)
     prior = torch.as_tensor(np.asarray(prior), dtype=torch.float64)
     B = syn.shape[0]
@@ -82,6 +96,7 @@ def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0):
     v2c = lam(Pi0[g.var].expand(B, g.E, 3), g.own, g.anti).clamp(-clip, clip)   # eq. (init)
     Qprev = Pi0.expand(B, g.N, 3)
     Q = Qprev
+    gm = torch.zeros(B, g.N, 3, dtype=torch.float64)
     for t in range(T):
         Pit = Pi0 if t == 0 else alpha[t] * Pi0 + (1.0 - alpha[t]) * Qprev
         # eq. (h_update): 2 atanh(prod_f tanh(m_f/2)) written with Gallager's
@@ -97,7 +112,11 @@ def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0):
         psign = sgn_pad[:, g.others].prod(-1)
         c2v = (w * sign * psign * phi(ext)).clamp(-clip, clip)
         S = torch.zeros(B, g.N, 3, dtype=torch.float64).index_add(1, g.var, c2v[..., None] * g.anti)
-        Q = Pit.expand(B, g.N, 3) + S                                              # eq. (p_update)
+        if model == "momentum":
+            gm = gamma[t] * gm + (1.0 - gamma[t]) * (Qprev - Pi0 - S)              # eqs. (mombp1), (mombp3)
+            Q = Qprev - alpha[t] * gm                                              # eq. (mombp2)
+        else:
+            Q = Pit.expand(B, g.N, 3) + S                                          # eq. (p_update)
         q_own = Q[:, g.var, :] - c2v[..., None] * g.anti                           # Q minus own message
         new = lam(q_own, g.own, g.anti).clamp(-clip, clip)
         v2c = (1.0 - beta[t]) * new + beta[t] * v2c
@@ -114,12 +133,18 @@ def loss(Q: torch.Tensor, err) -> torch.Tensor:
     return -logp.gather(-1, err[..., None]).squeeze(-1).mean()
 
 
-def loss_and_grads(H, syn, err, prior, alpha, beta, w, T: int, clip: float = 30.0):
-    """(loss, d loss / d alpha, d beta, d w) in float64 by autograd."""
+def loss_and_grads(H, syn, err, prior, alpha, beta, w, T: int, clip: float = 30.0, model: str = "ewainit",
+                   gamma=None):
+    """(loss, d loss / d alpha, d beta, d w) in float64 by autograd; for
+    model "momentum" also d loss / d gamma, as a fifth element."""
     g = Graph(H)
     a = torch.tensor(np.asarray(alpha, dtype=np.float64), requires_grad=True)
     b = torch.tensor(np.asarray(beta, dtype=np.float64), requires_grad=True)
     ww = torch.tensor(np.asarray(w, dtype=np.float64), requires_grad=True)
-    L = loss(forward(g, syn, prior, a, b, ww, T, clip), err)
+    gm = None if gamma is None else torch.tensor(np.asarray(gamma, dtype=np.float64), requires_grad=True)
+    L = loss(forward(g, syn, prior, a, b, ww, T, clip, model=model, gamma=gm), err)
     L.backward()
-    return float(L), a.grad.numpy(), b.grad.numpy(), ww.grad.numpy()
+    out = (float(L), a.grad.numpy(), b.grad.numpy(), ww.grad.numpy())
+    if model == "momentum":
+        out = out + (gm.grad.numpy(),)
+    return out

@@ -72,3 +72,51 @@ def test_gradients_match_finite_differences(case):
     for e in [0, 17, g.E - 1]:
         d = np.zeros(g.E); d[e] = h
         assert (f(alpha, beta, w + d) - f(alpha, beta, w - d)) / (2 * h) == pytest.approx(gw[e], rel=1e-5, abs=1e-9)
+
+
+@pytest.mark.parametrize("alpha,gamma", [(0.5, 0.0), (0.7, 0.3)])
+def test_momentum_model_matches_c_oracle_trace(case, alpha, gamma):
+    """The Momentum model at constant alpha, gamma, beta = 0, w = 1 is
+    Momentum-BP (eqs. (mombp1), (mombp2), (mombp5)): same posterior as the
+    C oracle."""
+    H, err, syn, prior = case
+    T = 8
+    g = unrolled.Graph(H)
+    Q = unrolled.forward(g, syn, prior, torch.full((T,), alpha, dtype=torch.float64), torch.zeros(T, dtype=torch.float64),
+                         torch.ones(g.E, dtype=torch.float64), T, model="momentum",
+                         gamma=torch.full((T,), gamma, dtype=torch.float64))
+    for b in range(syn.shape[0]):
+        tr = oracle.trace(H, syn[b], prior, variant="momentum", alpha=alpha, gamma=gamma, T=T)
+        assert np.allclose(Q[b].numpy(), tr["Q"][-1], rtol=1e-8, atol=1e-5)
+
+
+def test_momentum_model_gradients_match_finite_differences(case):
+    H, err, syn, prior = case
+    T = 6
+    g = unrolled.Graph(H)
+    rng = np.random.default_rng(4)
+    alpha = 0.6 + 0.1 * rng.standard_normal(T)
+    gamma = 0.3 + 0.1 * rng.standard_normal(T)
+    beta = 0.1 * np.abs(rng.standard_normal(T))
+    w = 1.0 + 0.1 * rng.standard_normal(g.E)
+    L, ga, gb, gw, gg = unrolled.loss_and_grads(H, syn[:2], err[:2], prior, alpha, beta, w, T, model="momentum",
+                                                gamma=gamma)
+
+    def f(a, b, ww, gm):
+        return float(unrolled.loss(unrolled.forward(g, syn[:2], prior, torch.tensor(a), torch.tensor(b),
+                                                    torch.tensor(ww), T, model="momentum", gamma=torch.tensor(gm)),
+                                   err[:2]))
+
+    h = 1e-6
+    for k in [0, 2, T - 1]:
+        d = np.zeros(T); d[k] = h
+        assert (f(alpha + d, beta, w, gamma) - f(alpha - d, beta, w, gamma)) / (2 * h) == pytest.approx(
+            ga[k], rel=1e-5, abs=1e-9)
+        assert (f(alpha, beta, w, gamma + d) - f(alpha, beta, w, gamma - d)) / (2 * h) == pytest.approx(
+            gg[k], rel=1e-5, abs=1e-9)
+        assert (f(alpha, beta + d, w, gamma) - f(alpha, beta - d, w, gamma)) / (2 * h) == pytest.approx(
+            gb[k], rel=1e-5, abs=1e-9)
+    for e in [0, 17, g.E - 1]:
+        d = np.zeros(g.E); d[e] = h
+        assert (f(alpha, beta, w + d, gamma) - f(alpha, beta, w - d, gamma)) / (2 * h) == pytest.approx(
+            gw[e], rel=1e-5, abs=1e-9)
