@@ -53,12 +53,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
-    ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve", "train", "aewa"],
+    ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve", "train", "aewa", "serial"],
                     help="toric15: the headline sweep; mixed: many codes in one batched launch; "
                          "serve: continuous-batching server on a Poisson request stream; "
                          "train: differentiable unrolled EWAInit-BP (forward + backward kernels); "
-                         "aewa: EWAInit-BP vs AEWA-BP on planar L = 3, 7, 11 (Appendix C)")
+                         "aewa: EWAInit-BP vs AEWA-BP on planar L = 3, 7, 11 (Appendix C); "
+                         "serial: serial vs parallel schedule on planar d=7 and toric d=15")
     ap.add_argument("--loads", default="1e4,1e5,1e6,1e7", help="offered loads (requests/s) for --workload serve")
+    ap.add_argument("--train-model", default="ewainit", choices=["ewainit", "momentum"],
+                    help="unrolled model for --workload train")
     return ap.parse_args()
 
 
@@ -607,6 +610,79 @@ def run_aewa(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serial schedule workload
+
+SERIAL_CODES = (("planar", 7), ("toric", 15))
+SERIAL_P = (0.04, 0.08, 0.12)
+SERIAL_SHOTS = 100_000
+
+
+def run_serial(args, rank, world):
+    """Plain BP and EWAInit-BP (alpha 0.5) under the serial schedule of
+    Algorithm 1 (bpq_decode_serial) and the parallel schedule, max 100
+    iterations: shots/s, LER, convergence and iterations per point."""
+    import torch
+
+    import paper_2407_11523_gb300 as bpq
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    B = SERIAL_SHOTS
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    work = bpq.workspace(dev)
+    rows, timed_ms, launches = [], 0.0, 0
+    for code, d in SERIAL_CODES:
+        t = bpq.Tanner(code, d).upload()
+        for k, p in enumerate(SERIAL_P):
+            ch = (p / 3, p / 3, p / 3)
+            err, syn = bpq.sample(t, *ch, seed=SEED + 500 + 10 * d + k, shot0=rank * B, B=B)
+            prior = bpq.prior_tensor(t, *ch)
+            out = (torch.empty((B, t.N), dtype=torch.uint8, device=dev), torch.empty(B, dtype=torch.uint8, device=dev),
+                   torch.empty(B, dtype=torch.uint8, device=dev))
+            row = {"code": f"{code} d={d}", "p": p}
+            for v in ("plain", "ewainit"):
+                params = bpq.make_params(v, **({"alpha": 0.5} if v == "ewainit" else {}))
+                for sched in ("serial", "parallel"):
+                    for _ in range(args.warmup):
+                        bpq.decode(t, syn, prior, v, params=params, max_iter=MAX_ITER, out=out, work=work,
+                                   schedule=sched)
+                    torch.cuda.synchronize()
+                    barrier(world)
+                    ms = 0.0
+                    for s_ in range(args.steps):
+                        flush.fill_(s_ & 0xFF)  # L2 flush between timed launches (outside the events)
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        bpq.decode(t, syn, prior, v, params=params, max_iter=MAX_ITER, out=out, work=work,
+                                   schedule=sched)
+                        b.record(stream)
+                        b.synchronize()
+                        ms += a.elapsed_time(b)
+                        launches += sched == "serial" and v == "ewainit"
+                    ms = reduce_max(ms, world)
+                    if sched == "serial" and v == "ewainit":
+                        timed_ms += ms
+                    fail = bpq.check_logical(t, err, out[0])
+                    row[f"{v}_{sched}"] = {
+                        "shots_per_s": reduce_sum(float(B * args.steps), world) / (ms / 1e3),
+                        "ler": reduce_sum(float((fail > 0).sum().item()), world) / (B * world),
+                        "converged_frac": float(out[1].float().mean().item()),
+                        "avg_iterations": float(out[2].float().mean().item())}
+            rows.append(row)
+    if rank == 0:
+        shots = float(B * args.steps * len(SERIAL_CODES) * len(SERIAL_P) * world)
+        line = {"metric": "serial-schedule EWAInit-BP decoded shots/s (planar d=7, toric d=15; p 0.04, 0.08, 0.12)",
+                "value": shots / (timed_ms / 1e3), "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": timed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"planar d=7 and toric d=15, depolarising p in {list(SERIAL_P)}, {B} shots "
+                                       f"per point per rank, max_iter {MAX_ITER}; plain and EWAInit (alpha 0.5) BP "
+                                       "under the serial and the parallel schedule",
+                           "l2": "a 256 MB buffer is written between timed launches"},
+                "points": rows, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving workload
 
 SERVE_CODES = [(k, d) for k in ("planar", "xzzx") for d in range(5, 32, 2)]
@@ -689,21 +765,27 @@ def run_train(args, rank, world):
     # a fresh batch every step (Philox shot offsets advance), drawn before timing
     n_batches = args.warmup + args.steps + 100
     pool = [draw(SEED + 3000, (rank * n_batches + k) * (B // len(ps)), B // len(ps)) for k in range(n_batches)]
+    model = args.train_model
+    mom = model == "momentum"
+    # start at the paper's parameters: EWAInit alpha 0.5; Momentum alpha 0.5, gamma 0
     a = torch.full((T,), 0.5, device="cuda", requires_grad=True)
     b = torch.zeros(T, device="cuda", requires_grad=True)
     w = torch.ones(t.E, device="cuda", requires_grad=True)
-    opt = torch.optim.Adam([a, b, w], lr=0.01)
+    g = torch.zeros(T, device="cuda", requires_grad=True) if mom else None
+    opt = torch.optim.Adam([a, b, w] + ([g] if mom else []), lr=0.01)
     it = iter(pool)
 
     def step():
         err, syn = next(it)
         opt.zero_grad()
-        L = bpq.unrolled_loss(t, syn, err, prior, a, b, w, T=T, ckpt_every=K)
+        L = bpq.unrolled_loss(t, syn, err, prior, a, b, w, T=T, ckpt_every=K, model=model, gamma=g)
         L.backward()
         opt.step()
         with torch.no_grad():
             a.clamp_(0.0, 1.0)
             b.clamp_(0.0, 0.95)
+            if mom:
+                g.clamp_(0.0, 0.95)
         return L.detach()
 
     stream = torch.cuda.current_stream()
@@ -729,13 +811,14 @@ def run_train(args, rank, world):
         fail = bpq.check_logical(t, err_t, est.to(torch.uint8).contiguous())
         return float((fail > 0).float().mean())
 
-    def ler_early_exit(aa, bb, ww):
-        # Algorithm 2's stopping rule on the unrolled decoder: each shot takes
-        # the decision of the first iteration whose decision satisfies the
-        # syndrome (else that of iteration T)
+    def ler_early_exit(aa, bb, ww, gg):
+        # the stopping rule of Algorithms 1 and 2 on the unrolled decoder: each
+        # shot takes the decision of the first iteration whose decision
+        # satisfies the syndrome (else that of iteration T)
         outcome = torch.full((err_t.shape[0],), 255, dtype=torch.uint8, device=err_t.device)
         for Tp in range(1, T + 1):
-            Q, _ = bpq.unrolled_posterior(t, syn_t, err_t, prior, aa[:Tp], bb[:Tp], ww, T=Tp, ckpt_every=Tp)
+            Q, _ = bpq.unrolled_posterior(t, syn_t, err_t, prior, aa[:Tp], bb[:Tp], ww, T=Tp, ckpt_every=Tp,
+                                          model=model, gamma=gg[:Tp] if gg is not None else None)
             allpos = (Q > 0).all(-1)
             est = torch.where(allpos, torch.zeros_like(allpos, dtype=torch.long), 1 + Q.argmin(-1))
             f = bpq.check_logical(t, err_t, est.to(torch.uint8).contiguous())
@@ -744,30 +827,34 @@ def run_train(args, rank, world):
         return float((outcome > 0).float().mean())
 
     with torch.no_grad():
-        Qtr, Ltr = bpq.unrolled_posterior(t, syn_t, err_t, prior, a, b, w, T=T)
+        g0 = torch.zeros_like(a) if mom else None
+        gt = g.detach() if mom else None
+        Qtr, Ltr = bpq.unrolled_posterior(t, syn_t, err_t, prior, a, b, w, T=T, model=model, gamma=gt)
         Q0, L0 = bpq.unrolled_posterior(t, syn_t, err_t, prior, torch.full_like(a, 0.5), torch.zeros_like(b),
-                                        torch.ones_like(w), T=T)
-        ler_ee = {"trained": ler_early_exit(a.detach(), b.detach(), w.detach()),
-                  "untrained": ler_early_exit(torch.full_like(a, 0.5), torch.zeros_like(b), torch.ones_like(w))}
-    est_k, conv_k, _ = bpq.decode(t, syn_t, prior, "ewainit", max_iter=T, alpha=0.5)
+                                        torch.ones_like(w), T=T, model=model, gamma=g0)
+        ler_ee = {"trained": ler_early_exit(a.detach(), b.detach(), w.detach(), gt),
+                  "untrained": ler_early_exit(torch.full_like(a, 0.5), torch.zeros_like(b), torch.ones_like(w), g0)}
+    est_k, conv_k, _ = bpq.decode(t, syn_t, prior, model, max_iter=T, alpha=0.5, **({"gamma": 0.0} if mom else {}))
     ler_kernel = float((bpq.check_logical(t, err_t, est_k) > 0).float().mean())
     if rank == 0:
-        line = {"metric": "differentiable unrolled EWAInit-BP: training shots/s (forward + hand-written backward)",
+        name = "Momentum-BP" if mom else "EWAInit-BP"
+        line = {"metric": f"differentiable unrolled {name}: training shots/s (forward + hand-written backward)",
                 "value": B / sec, "unit": "shots/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"planar d={d} (N={t.N}, E={t.E}), T={T}, checkpoints every {K}, batch {B} "
                                        f"depolarising errors at p in {[round(float(x), 3) for x in ps]}, "
                                        f"prior p={p0:.3f}; "
-                                       "trainable alpha_t, beta_t (T each) and w_e (E); Adam lr 0.01, a fresh "
-                                       "Philox batch every step, 108 steps"},
+                                       "trainable alpha_t, beta_t" + (", gamma_t" if mom else "") +
+                                       " (T each) and w_e (E); Adam lr 0.01, a fresh Philox batch every step, "
+                                       "108 steps", "model": model},
                 "train_loss_first_last": [losses[0], losses[-1]],
                 "held_out_loss": {"trained": float(Ltr), "untrained": float(L0)},
                 "held_out_ler": {"trained_unrolled": ler_from_Q(Qtr), "untrained_unrolled": ler_from_Q(Q0),
                                  "trained_unrolled_early_exit": ler_ee["trained"],
                                  "untrained_unrolled_early_exit": ler_ee["untrained"],
-                                 "ewainit_kernel_early_exit": ler_kernel, "shots": int(err_t.shape[0])},
-                "gpu_launches": 6 * args.steps}
+                                 f"{model}_kernel_early_exit": ler_kernel, "shots": int(err_t.shape[0])},
+                "gpu_launches": (7 if mom else 6) * args.steps}
         print(json.dumps(line), flush=True)
 
 def main():
@@ -781,6 +868,8 @@ def main():
         run_serve(args, rank, world)
     elif args.workload == "aewa":
         run_aewa(args, rank, world)
+    elif args.workload == "serial":
+        run_serial(args, rank, world)
     elif args.workload == "train":
         run_train(args, rank, world)
     else:

@@ -225,17 +225,46 @@ int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
                  uint8_t *iters_dev, void *work_dev, void *stream, int *threads_per_shot, int *shots_per_cta,
                  float *best_ms);
 
+/* ---------------------------------------------------------------- serial schedule */
+
+/* Decoding under the serial schedule of Algorithm 1 (Sec. III-A1): in each
+ * iteration the qubits are visited in index order and qubit j takes the
+ * c->v messages of its checks (eq. (h_update)) from the v->c messages as
+ * they stand (already updated in this iteration for the qubits before j),
+ * updates its posterior by the variant's rule and sends new v->c messages
+ * (eq. (v_update); eq. (mombp5) for Momentum and AdaGrad); the hard
+ * decision and syndrome test follow each full sweep.  The kernel runs the
+ * sweep's dependency levels in order, all qubits of a level at once, which
+ * gives the serial order's result exactly; one warp decodes one shot.
+ * variant: plain, Momentum, AdaGrad or EWAInit BP (EINVAL otherwise).
+ * Arguments, layouts, ownership, asynchrony and errors as bpq_decode; iters
+ * counts sweeps.  EINVAL also when one shot's state does not fit in shared
+ * memory (about 4600 edges for EWAInit-BP). */
+int bpq_decode_serial(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+                      const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
+                      uint8_t *iters_dev, void *work_dev, void *stream);
+
+/* Per-sweep record of the serial schedule, in bpq_decode_trace's layout:
+ * exactly T sweeps, no stopping rule; m_v2c_dev [B][T+1][E] holds each
+ * edge's v->c message as sent in that sweep, m_c2v_dev [B][T][E] the c->v
+ * message its qubit took. */
+int bpq_decode_serial_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+                            const bpq_params *params, int T, int B, float *m_v2c_dev, float *m_c2v_dev, float *Q_dev,
+                            uint8_t *dec_dev, void *work_dev, void *stream);
+
 /* ---------------------------------------------------------------- batched decoding */
 
 /* Many codes in one persistent launch (an interface addition; the paper
  * decodes one code at a time).  Each item is one code's batch: syndromes,
- * prior and outputs exactly as for bpq_decode.  All items share the variant,
- * parameters and max_iter.  The launch splits the items into tiles of
- * (shots per CTA of that code) x tile_shots shots, queued code by code; a
- * CTA of 512 threads decodes a tile with the code's own threads-per-shot
- * (from bpq_set_launch / bpq_autotune, else the default) and re-stages the
- * code's adjacency when the code changes.  Per-shot results equal those of
- * bpq_decode bit for bit. */
+ * prior and outputs exactly as for bpq_decode.  All items share the variant
+ * (plain, Momentum, AdaGrad or EWAInit BP), parameters and max_iter.  A CTA
+ * of 1024 threads works on one item at a time with that code's
+ * threads-per-shot (from bpq_set_launch / bpq_autotune, else the default;
+ * at most two nodes per thread): its shot groups take the item's shots one
+ * by one from a per-item counter until none are left, and the CTA then moves
+ * to another item with shots left, re-staging that code's adjacency.  CTAs
+ * start spread over the items in proportion to shots x edges.  Per-shot
+ * results equal those of bpq_decode bit for bit. */
 typedef struct {
     const bpq_tanner *tanner;  /* uploaded; all items on one device */
     const uint32_t *syn_dev;   /* [B][ceil(M/32)] */
@@ -246,22 +275,27 @@ typedef struct {
 
 typedef struct bpq_batch bpq_batch; /* opaque plan, library-owned */
 
-/* Device workspace needed by a plan of n_items items and total_shots shots. */
-size_t bpq_batch_workspace_bytes(int n_items, long total_shots, int tile_shots);
+/* Device workspace needed by a plan of n_items items (0 if n_items < 1). */
+size_t bpq_batch_workspace_bytes(int n_items);
 
-/* Build the plan: per-code descriptors and the tile list, copied into
- * work_dev (caller-owned, bpq_batch_workspace_bytes large, to stay untouched
- * while the plan is used).  Synchronizes `stream`.  Errors: EINVAL, ESTATE,
- * ECUDA.  Release with bpq_batch_free. */
+/* Build the plan: per-item counters, descriptors and the CTAs' starting
+ * items, copied into work_dev (caller-owned, bpq_batch_workspace_bytes
+ * large, to stay untouched while the plan is used).  Synchronizes `stream`.
+ * Errors: EINVAL (no items, a NULL buffer, a variant other than the four,
+ * max_iter outside [1, 255], too small a workspace), ESTATE (an item's
+ * tanner not uploaded, or items on different devices), ECUDA.  Release with
+ * bpq_batch_free. */
 int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const bpq_params *params, int max_iter,
-                   int tile_shots, void *work_dev, size_t work_bytes, void *stream, bpq_batch **out);
+                   void *work_dev, size_t work_bytes, void *stream, bpq_batch **out);
 
 /* Enqueue one run of the plan on `stream` (a counter reset and one kernel
  * launch; no host synchronization and no allocation, so the call can be
  * captured in a CUDA graph).  Runs of one plan must not overlap. */
 int bpq_batch_launch(const bpq_batch *b, void *stream);
 
-int bpq_batch_info(const bpq_batch *b, int *ctas, int *tiles, int *npt_max, long *shots);
+/* ctas: CTAs per launch; items: n_items; npt_max: the kernel's nodes per
+ * thread; shots: total shots.  Any pointer may be NULL. */
+int bpq_batch_info(const bpq_batch *b, int *ctas, int *items, int *npt_max, long *shots);
 void bpq_batch_free(bpq_batch *b);
 
 /* ---------------------------------------------------------------- serving */
@@ -284,8 +318,8 @@ size_t bpq_server_device_bytes(const bpq_tanner *const *codes, int n_codes, int 
  * float probabilities of code c.  Creates the lanes' streams, events and
  * pinned host staging.  Errors: EINVAL, ESTATE, ECUDA. */
 int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors_dev, int n_codes, int variant,
-                      const bpq_params *params, int max_iter, int n_lanes, int max_batch, int tile_shots,
-                      void *dev_mem, size_t dev_bytes, bpq_server **out);
+                      const bpq_params *params, int max_iter, int n_lanes, int max_batch, void *dev_mem,
+                      size_t dev_bytes, bpq_server **out);
 
 /* Serve a request trace in real time (host wall clock from the call):
  * request r is decoding code code[r], becomes available at arrival_s[r]
@@ -308,30 +342,43 @@ void bpq_server_free(bpq_server *s);
 
 /* ---------------------------------------------------------------- differentiable decoding */
 
-/* Unrolled EWAInit-BP with trainable parameters (an extension in the
+/* Unrolled decoders with trainable parameters (an extension in the
  * direction of neural BP named in the paper's conclusion): T flooding
- * iterations of Algorithm 2 without the stopping rule, where iteration t
- * uses its own EWA weight alpha_t (eq. (EWAInit)), damps the
- * variable-to-check messages as (1 - beta_t) lambda(...) + beta_t m^(t-1),
- * and scales each check-to-variable message by a weight w_e (E weights in
- * the check-major edge order of bpq_tanner_export).  alpha_t = alpha,
- * beta_t = 0, w_e = 1 is EWAInit-BP.  Loss: the mean over shots and qubits
- * of -log softmax(0, -Q_X, -Q_Y, -Q_Z)[true Pauli] of the final posterior.
- * Inputs: syn_dev [B][ceil(M/32)], err_dev [B][N] Pauli codes (the true
- * errors), prior_dev [N][3]; alpha_dev, beta_dev [T], w_dev [E] (device
- * float).  Codes of up to 1024 nodes; T <= 255.  The forward pass stores a
- * checkpoint every ckpt_every iterations in work_dev; bpq_train_backward
- * (same inputs, after the forward on the same workspace) recomputes each
- * segment from its checkpoint and writes d loss / d alpha, beta, w.
- * Results are deterministic.  Q_dev (optional) receives Q^(T) [B][N][3]. */
-size_t bpq_train_workspace_bytes(const bpq_tanner *t, int B, int T, int ckpt_every);
-int bpq_train_forward(const bpq_tanner *t, const uint32_t *syn_dev, const uint8_t *err_dev, const float *prior_dev,
-                      int B, int T, int ckpt_every, const float *alpha_dev, const float *beta_dev, const float *w_dev,
-                      float msg_clip, float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes, void *stream);
-int bpq_train_backward(const bpq_tanner *t, const uint32_t *syn_dev, const uint8_t *err_dev, const float *prior_dev,
-                       int B, int T, int ckpt_every, const float *alpha_dev, const float *beta_dev, const float *w_dev,
-                       float msg_clip, float *grad_alpha_dev, float *grad_beta_dev, float *grad_w_dev, void *work_dev,
-                       size_t work_bytes, void *stream);
+ * iterations without the stopping rule, where iteration t has its own
+ * parameters.
+ *   model BPQ_TRAIN_EWAINIT: EWAInit-BP (Algorithm 2) with EWA weight
+ *     alpha_t, Pi^(t) = alpha_t Pi^(0) + (1 - alpha_t) Q^(t-1) (eq. (EWAInit));
+ *   model BPQ_TRAIN_MOMENTUM: Momentum-BP (eqs. (mombp1)-(mombp3)) with step
+ *     alpha_t and momentum rate gamma_t, g^(t) = gamma_t g^(t-1) +
+ *     (1 - gamma_t)(Q^(t-1) - Pi^(0) - S^(t)), Q^(t) = Q^(t-1) - alpha_t g^(t).
+ * Both damp the variable-to-check messages as (1 - beta_t) lambda(...) +
+ * beta_t m^(t-1) and scale each check-to-variable message by a weight w_e
+ * (E weights in the check-major edge order of bpq_tanner_export).  Constant
+ * alpha (and gamma), beta_t = 0, w_e = 1 is EWAInit-BP (Momentum-BP).
+ * Loss: the mean over shots and qubits of -log softmax(0, -Q_X, -Q_Y,
+ * -Q_Z)[true Pauli] of the final posterior.  Inputs: syn_dev [B][ceil(M/32)],
+ * err_dev [B][N] Pauli codes (the true errors), prior_dev [N][3];
+ * alpha_dev, beta_dev, gamma_dev [T] (gamma ignored, may be NULL, for
+ * EWAInit), w_dev [E] (device float).  Codes of up to 1024 nodes; T <= 255.
+ * The forward pass stores a checkpoint every ckpt_every iterations in
+ * work_dev; bpq_train_backward (same inputs, after the forward on the same
+ * workspace) recomputes each segment from its checkpoint and writes
+ * d loss / d alpha, beta, w (and gamma for Momentum; grad_gamma_dev may be
+ * NULL for EWAInit).  Results are deterministic.  Q_dev (optional) receives
+ * Q^(T) [B][N][3].  Errors: EINVAL (unknown model, sizes, NULL buffers,
+ * too small a workspace, a checkpoint segment too long for shared memory),
+ * ESTATE, ECUDA. */
+enum bpq_train_model { BPQ_TRAIN_EWAINIT = 0, BPQ_TRAIN_MOMENTUM = 1 };
+size_t bpq_train_workspace_bytes(const bpq_tanner *t, int model, int B, int T, int ckpt_every);
+int bpq_train_forward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
+                      const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
+                      const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
+                      float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes, void *stream);
+int bpq_train_backward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
+                       const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
+                       const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
+                       float *grad_alpha_dev, float *grad_beta_dev, float *grad_gamma_dev, float *grad_w_dev,
+                       void *work_dev, size_t work_bytes, void *stream);
 
 /* ---------------------------------------------------------------- evaluation */
 

@@ -1,7 +1,7 @@
 """GB300-native GF(4) belief-propagation decoding of surface-code syndromes:
 plain LLR-BP4, Momentum-BP, AdaGrad-BP and EWAInit-BP under the flooding
-schedule (Chen, Yi, Liang, Wang, "Improved Belief Propagation Decoding
-Algorithms for Surface Codes").
+schedule, AEWA-BP, and the serial schedule (Chen, Yi, Liang, Wang,
+"Improved Belief Propagation Decoding Algorithms for Surface Codes").
 
 The compute lives in libbpq.so (CUDA for sm_103a, C ABI in include/bpq.h);
 this package is its thin Python binding.

@@ -62,6 +62,8 @@ def lib():
             "bpq_decode_host_bytes": (sz, [P, i]),
             "bpq_decode_host": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, sz, P]),
             "bpq_decode_trace": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, P, P]),
+            "bpq_decode_serial": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, P]),
+            "bpq_decode_serial_trace": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, P, P]),
             "bpq_decode_host_noalloc": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P]),
             "bpq_decode_host_noalloc_max_shots": (i, [P]),
             "bpq_set_launch": (i, [P, i, i]),
@@ -70,19 +72,19 @@ def lib():
             "bpq_get_launch": (i, [P, pi, pi, pi]),
             "bpq_check_logical": (i, [P, P, P, i, P, P]),
             "bpq_probe_peak": (i, [i, i, i, i, P, P]),
-            "bpq_batch_workspace_bytes": (sz, [i, ctypes.c_long, i]),
-            "bpq_batch_plan": (i, [P, i, i, ctypes.POINTER(Params), i, i, P, sz, P, PP]),
+            "bpq_batch_workspace_bytes": (sz, [i]),
+            "bpq_batch_plan": (i, [P, i, i, ctypes.POINTER(Params), i, P, sz, P, PP]),
             "bpq_batch_launch": (i, [P, P]),
             "bpq_batch_info": (i, [P, pi, pi, pi, ctypes.POINTER(ctypes.c_long)]),
             "bpq_batch_free": (None, [P]),
             "bpq_server_device_bytes": (sz, [P, i, i, i]),
-            "bpq_server_create": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, i, P, sz, PP]),
+            "bpq_server_create": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, P, sz, PP]),
             "bpq_server_replay": (i, [P, i, P, P, P, P, P, P, P, P, P, pi]),
             "bpq_server_stats": (i, [P, ctypes.POINTER(ctypes.c_long)]),
             "bpq_server_free": (None, [P]),
-            "bpq_train_workspace_bytes": (sz, [P, i, i, i]),
-            "bpq_train_forward": (i, [P, P, P, P, i, i, i, P, P, P, ctypes.c_float, P, P, P, sz, P]),
-            "bpq_train_backward": (i, [P, P, P, P, i, i, i, P, P, P, ctypes.c_float, P, P, P, P, sz, P]),
+            "bpq_train_workspace_bytes": (sz, [P, i, i, i, i]),
+            "bpq_train_forward": (i, [P, i, P, P, P, i, i, i, P, P, P, P, ctypes.c_float, P, P, P, sz, P]),
+            "bpq_train_backward": (i, [P, i, P, P, P, i, i, i, P, P, P, P, ctypes.c_float, P, P, P, P, P, sz, P]),
             "bpq_last_error": (ctypes.c_char_p, []),
             "bpq_version": (i, []),
         }
@@ -249,9 +251,11 @@ def prior_tensor(tanner: Tanner, px, py, pz, device=None) -> torch.Tensor:
 
 
 def decode(tanner: Tanner, syn, prior, variant="ewainit", params=None, max_iter=50, out=None, work=None,
-           stream=None, **param_kw):
-    """Decode packed syndromes (B, W) int32 on the device.  Returns
-    (est (B, N) uint8, conv (B,) uint8, iters (B,) uint8) device tensors."""
+           stream=None, schedule="parallel", **param_kw):
+    """Decode packed syndromes (B, W) int32 on the device.  schedule:
+    "parallel" (flooding, bpq_decode) or "serial" (Algorithm 1's sweep,
+    bpq_decode_serial).  Returns (est (B, N) uint8, conv (B,) uint8,
+    iters (B,) uint8) device tensors."""
     tanner.upload()
     v = VARIANTS.get(variant, variant)
     p = params if params is not None else make_params(v, **param_kw)
@@ -265,8 +269,9 @@ def decode(tanner: Tanner, syn, prior, variant="ewainit", params=None, max_iter=
     if work is None:
         work = workspace(dev)
     assert syn.is_contiguous() and prior.is_contiguous() and prior.dtype == torch.float32
-    _check(lib().bpq_decode(tanner.handle, _ptr(syn), _ptr(prior), v, ctypes.byref(p), max_iter, B, _ptr(est),
-                            _ptr(conv), _ptr(iters), _ptr(work), _stream(stream)), "bpq_decode")
+    fn = {"parallel": "bpq_decode", "serial": "bpq_decode_serial"}[schedule]
+    _check(getattr(lib(), fn)(tanner.handle, _ptr(syn), _ptr(prior), v, ctypes.byref(p), max_iter, B, _ptr(est),
+                              _ptr(conv), _ptr(iters), _ptr(work), _stream(stream)), fn)
     return est, conv, iters
 
 
@@ -302,7 +307,8 @@ def decode_host(tanner: Tanner, syn_host, prior_host, variant="ewainit", params=
     return est, conv, iters
 
 
-def decode_trace(tanner: Tanner, syn, prior, variant="plain", T=5, params=None, stream=None, **param_kw):
+def decode_trace(tanner: Tanner, syn, prior, variant="plain", T=5, params=None, stream=None, schedule="parallel",
+                 **param_kw):
     """Run exactly T iterations and return the per-iteration record:
     m_v2c (B, T+1, E), m_c2v (B, T, E), Q (B, T, N, 3), dec (B, T, N)."""
     tanner.upload()
@@ -315,9 +321,10 @@ def decode_trace(tanner: Tanner, syn, prior, variant="plain", T=5, params=None, 
                Q=torch.zeros((B, T, tanner.N, 3), dtype=torch.float32, device=dev),
                dec=torch.zeros((B, T, tanner.N), dtype=torch.uint8, device=dev))
     work = workspace(dev)
-    _check(lib().bpq_decode_trace(tanner.handle, _ptr(syn), _ptr(prior), v, ctypes.byref(p), T, B,
-                                  _ptr(rec["m_v2c"]), _ptr(rec["m_c2v"]), _ptr(rec["Q"]), _ptr(rec["dec"]),
-                                  _ptr(work), _stream(stream)), "bpq_decode_trace")
+    fn = {"parallel": "bpq_decode_trace", "serial": "bpq_decode_serial_trace"}[schedule]
+    _check(getattr(lib(), fn)(tanner.handle, _ptr(syn), _ptr(prior), v, ctypes.byref(p), T, B,
+                              _ptr(rec["m_v2c"]), _ptr(rec["m_c2v"]), _ptr(rec["Q"]), _ptr(rec["dec"]),
+                              _ptr(work), _stream(stream)), fn)
     return rec
 
 
@@ -362,7 +369,7 @@ class BatchPlan:
     The plan owns its outputs (est, conv, iters per item) and its device
     workspace; run() enqueues one launch (capturable in a CUDA graph)."""
 
-    def __init__(self, items, variant="ewainit", params=None, max_iter=100, tile_shots=64, stream=None,
+    def __init__(self, items, variant="ewainit", params=None, max_iter=100, stream=None,
                  **param_kw):
         v = VARIANTS.get(variant, variant)
         self.params = params if params is not None else make_params(v, **param_kw)
@@ -381,11 +388,11 @@ class BatchPlan:
             arr[k] = BatchItem(t.handle.value, syn.data_ptr(), prior.data_ptr(), B, out[0].data_ptr(),
                                out[1].data_ptr(), out[2].data_ptr())
             total += B
-        nbytes = lib().bpq_batch_workspace_bytes(len(items), total, tile_shots)
+        nbytes = lib().bpq_batch_workspace_bytes(len(items))
         self.work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         self._h = ctypes.c_void_p()
-        _check(lib().bpq_batch_plan(arr, len(items), v, ctypes.byref(self.params), max_iter, tile_shots,
-                                    _ptr(self.work), nbytes, _stream(stream), ctypes.byref(self._h)), "bpq_batch_plan")
+        _check(lib().bpq_batch_plan(arr, len(items), v, ctypes.byref(self.params), max_iter, _ptr(self.work), nbytes,
+                                    _stream(stream), ctypes.byref(self._h)), "bpq_batch_plan")
         self.total_shots = total
 
     def run(self, stream=None):
@@ -396,7 +403,7 @@ class BatchPlan:
         c, t, n, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_long()
         _check(lib().bpq_batch_info(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(n), ctypes.byref(s)),
                "bpq_batch_info")
-        return dict(ctas=c.value, tiles=t.value, npt_max=n.value, shots=s.value)
+        return dict(ctas=c.value, items=t.value, npt_max=n.value, shots=s.value)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -411,7 +418,7 @@ class Server:
     real time and returns per-request outputs and completion times."""
 
     def __init__(self, codes, priors, variant="ewainit", params=None, max_iter=100, n_lanes=4, max_batch=4096,
-                 tile_shots=16, **param_kw):
+                 **param_kw):
         v = VARIANTS.get(variant, variant)
         self.params = params if params is not None else make_params(v, **param_kw)
         self.codes = [t.upload() for t in codes]
@@ -423,7 +430,7 @@ class Server:
         self.mem = torch.empty(nbytes, dtype=torch.uint8, device=self.priors[0].device)
         self._h = ctypes.c_void_p()
         _check(lib().bpq_server_create(harr, parr, n, v, ctypes.byref(self.params), max_iter, n_lanes, max_batch,
-                                       tile_shots, _ptr(self.mem), nbytes, ctypes.byref(self._h)), "bpq_server_create")
+                                       _ptr(self.mem), nbytes, ctypes.byref(self._h)), "bpq_server_create")
 
     def replay(self, code, arrival_s, syn_list):
         """code: (R,) int; arrival_s: (R,) float, non-decreasing; syn_list:
@@ -463,53 +470,73 @@ class Server:
             self._h = None
 
 
-class _UnrolledEWAInit(torch.autograd.Function):
-    """Loss of the unrolled EWAInit-BP decoder as a function of its
-    parameters (alpha, beta, w); forward and backward run in libbpq's CUDA
-    kernels (bpq_train_forward / bpq_train_backward)."""
+TRAIN_MODELS = {"ewainit": 0, "momentum": 1}
+
+
+class _Unrolled(torch.autograd.Function):
+    """Loss of an unrolled decoder (model EWAInit or Momentum) as a function
+    of its parameters (alpha, beta, w, gamma); forward and backward run in
+    libbpq's CUDA kernels (bpq_train_forward / bpq_train_backward)."""
 
     @staticmethod
-    def forward(ctx, alpha, beta, w, tanner, syn, err, prior, T, ckpt_every, msg_clip):
+    def forward(ctx, alpha, beta, w, gamma, model, tanner, syn, err, prior, T, ckpt_every, msg_clip):
         alpha, beta, w = alpha.contiguous().float(), beta.contiguous().float(), w.contiguous().float()
+        gamma = gamma.contiguous().float() if gamma is not None else None
         B = syn.shape[0]
-        nbytes = lib().bpq_train_workspace_bytes(tanner.handle, B, T, ckpt_every)
+        nbytes = lib().bpq_train_workspace_bytes(tanner.handle, model, B, T, ckpt_every)
         work = torch.empty(nbytes, dtype=torch.uint8, device=syn.device)
         loss = torch.empty(1, dtype=torch.float32, device=syn.device)
-        _check(lib().bpq_train_forward(tanner.handle, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every,
-                                       _ptr(alpha), _ptr(beta), _ptr(w), msg_clip, _ptr(loss), None, _ptr(work),
-                                       nbytes, _stream(None)), "bpq_train_forward")
-        ctx.save_for_backward(alpha, beta, w)
-        ctx.rest = (tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes)
+        _check(lib().bpq_train_forward(tanner.handle, model, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every,
+                                       _ptr(alpha), _ptr(beta), _ptr(gamma) if gamma is not None else None, _ptr(w),
+                                       msg_clip, _ptr(loss), None, _ptr(work), nbytes, _stream(None)),
+               "bpq_train_forward")
+        ctx.save_for_backward(alpha, beta, w, *( [gamma] if gamma is not None else []))
+        ctx.rest = (model, tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes)
         return loss[0]
 
     @staticmethod
     def backward(ctx, gout):
-        alpha, beta, w = ctx.saved_tensors
-        tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes = ctx.rest
+        saved = ctx.saved_tensors
+        alpha, beta, w = saved[:3]
+        gamma = saved[3] if len(saved) > 3 else None
+        model, tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes = ctx.rest
         ga, gb, gw = torch.empty_like(alpha), torch.empty_like(beta), torch.empty_like(w)
-        _check(lib().bpq_train_backward(tanner.handle, _ptr(syn), _ptr(err), _ptr(prior), syn.shape[0], T,
-                                        ckpt_every, _ptr(alpha), _ptr(beta), _ptr(w), msg_clip, _ptr(ga), _ptr(gb),
-                                        _ptr(gw), _ptr(work), nbytes, _stream(None)), "bpq_train_backward")
-        return ga * gout, gb * gout, gw * gout, None, None, None, None, None, None, None
+        gg = torch.empty_like(gamma) if gamma is not None else None
+        _check(lib().bpq_train_backward(tanner.handle, model, _ptr(syn), _ptr(err), _ptr(prior), syn.shape[0], T,
+                                        ckpt_every, _ptr(alpha), _ptr(beta),
+                                        _ptr(gamma) if gamma is not None else None, _ptr(w), msg_clip, _ptr(ga),
+                                        _ptr(gb), _ptr(gg) if gg is not None else None, _ptr(gw), _ptr(work), nbytes,
+                                        _stream(None)), "bpq_train_backward")
+        return (ga * gout, gb * gout, gw * gout, gg * gout if gg is not None else None,
+                None, None, None, None, None, None, None, None)
 
 
-def unrolled_loss(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0):
-    """Differentiable loss of the unrolled EWAInit-BP decoder (see
-    bpq_train_forward); gradients flow to alpha (T,), beta (T,) and w (E,)."""
+def unrolled_loss(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0,
+                  model="ewainit", gamma=None):
+    """Differentiable loss of the unrolled decoder (see bpq_train_forward):
+    model "ewainit" (EWA weights alpha) or "momentum" (steps alpha, rates
+    gamma); gradients flow to alpha (T,), beta (T,), w (E,) and gamma (T,)."""
     tanner.upload()
-    return _UnrolledEWAInit.apply(alpha, beta, w, tanner, syn, err, prior, T, ckpt_every, msg_clip)
+    m = TRAIN_MODELS[model]
+    if m == 1 and gamma is None:
+        raise BPQError("the Momentum model needs gamma")
+    return _Unrolled.apply(alpha, beta, w, gamma if m == 1 else None, m, tanner, syn, err, prior, T, ckpt_every,
+                           msg_clip)
 
 
-def unrolled_posterior(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0):
+def unrolled_posterior(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0,
+                       model="ewainit", gamma=None):
     """Final posterior Q^(T) (B, N, 3) and the loss of the unrolled decoder."""
     tanner.upload()
+    m = TRAIN_MODELS[model]
     B = syn.shape[0]
-    nbytes = lib().bpq_train_workspace_bytes(tanner.handle, B, T, ckpt_every)
+    nbytes = lib().bpq_train_workspace_bytes(tanner.handle, m, B, T, ckpt_every)
     work = torch.empty(nbytes, dtype=torch.uint8, device=syn.device)
     loss = torch.empty(1, dtype=torch.float32, device=syn.device)
     Q = torch.empty((B, tanner.N, 3), dtype=torch.float32, device=syn.device)
     a, b, ww = alpha.contiguous().float(), beta.contiguous().float(), w.contiguous().float()
-    _check(lib().bpq_train_forward(tanner.handle, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every, _ptr(a),
-                                   _ptr(b), _ptr(ww), msg_clip, _ptr(loss), _ptr(Q), _ptr(work), nbytes,
-                                   _stream(None)), "bpq_train_forward")
+    g = gamma.contiguous().float() if gamma is not None else None
+    _check(lib().bpq_train_forward(tanner.handle, m, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every, _ptr(a),
+                                   _ptr(b), _ptr(g) if g is not None else None, _ptr(ww), msg_clip, _ptr(loss),
+                                   _ptr(Q), _ptr(work), nbytes, _stream(None)), "bpq_train_forward")
     return Q, loss[0]

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libbpq.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "batch.cu", "server.cu", "train.cu", "decode.cu", "decode_plain.cu", "decode_momentum.cu", "decode_adagrad.cu",
-           "decode_ewainit.cu", "decode_aewa.cu", "tanner.cpp"]
+           "decode_ewainit.cu", "decode_aewa.cu", "serial.cu", "tanner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

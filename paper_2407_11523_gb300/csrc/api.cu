@@ -247,10 +247,14 @@ int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prio
     a.W = (t->M + 31) / 32;
     a.B = B;
     a.max_iter = max_iter;
-    a.alpha = p.alpha;
+    // the kernel keeps log-likelihoods in bits: AdaGrad's step alpha and eps
+    // are log-likelihoods too, the EWA and momentum weights are pure numbers
+    const float log2e = 1.4426950408889634f;
+    a.alpha = variant == BPQ_ADAGRAD ? p.alpha * log2e : p.alpha;
     a.gamma = p.gamma;
-    a.eps = p.eps;
+    a.eps = p.eps * log2e;
     a.clip = p.msg_clip;
+    a.clip2 = p.msg_clip * log2e;
     a.delta_clip = delta_of_clip(p.msg_clip);
     a.phi_clip = phi_of_clip(p.msg_clip);
     a.ada_from1 = p.adagrad_g_from_iter1 ? 1 : 0;
@@ -282,7 +286,8 @@ int bpq_tanner_upload(bpq_tanner *t, int device) {
     const size_t o_log = o_ptr + al(sizeof(int32_t) * t->chk_ptr.size());
     const size_t o_tab2 = o_log + al(t->logicals.size() + 1);
     const size_t o_canon2 = o_tab2 + al(t->table_split.size());
-    const size_t total = o_canon2 + al(sizeof(int32_t) * t->var_canon_split.size());
+    const size_t o_serial = o_canon2 + al(sizeof(int32_t) * t->var_canon_split.size());
+    const size_t total = o_serial + al(t->serial.size());
     void *blob = nullptr;
     rc = bpq::cuda_check(cudaMalloc(&blob, total), "cudaMalloc");
     if (rc) return rc;
@@ -299,6 +304,8 @@ int bpq_tanner_upload(bpq_tanner *t, int device) {
     if (e == cudaSuccess && t->split)
         e = cudaMemcpy(b + o_canon2, t->var_canon_split.data(), sizeof(int32_t) * t->var_canon_split.size(),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t->serial.empty())
+        e = cudaMemcpy(b + o_serial, t->serial.data(), t->serial.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
         return bpq::cuda_check(e, "cudaMemcpy");
@@ -312,6 +319,7 @@ int bpq_tanner_upload(bpq_tanner *t, int device) {
     t->d_logicals = t->logicals.empty() ? nullptr : b + o_log;
     t->d_table_split = t->split ? b + o_tab2 : nullptr;
     t->d_var_canon_split = t->split ? reinterpret_cast<const int32_t *>(b + o_canon2) : nullptr;
+    t->d_serial = b + o_serial;
     return BPQ_OK;
 }
 

@@ -1,8 +1,8 @@
 // Batched decoding of many codes in one persistent launch (bpq_batch_*).
-// The plan (per-code descriptors and the tile list) is built on the host and
-// copied once into the caller's device workspace; bpq_batch_launch then only
-// enqueues a counter reset and the kernel, so it can be captured in a CUDA
-// graph and replayed.
+// The plan (per-item descriptors and each CTA's starting item) is built on
+// the host and copied once into the caller's device workspace;
+// bpq_batch_launch then only enqueues a counter reset and the kernel, so it
+// can be captured in a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,9 +33,22 @@ BatchKernelFn pick_batch_kernel(int variant, int npt) {
         case BPQ_MOMENTUM: return pick_momentum_batch(npt);
         case BPQ_ADAGRAD: return pick_adagrad_batch(npt);
         case BPQ_EWAINIT: return pick_ewainit_batch(npt);
-        case BPQ_AEWA: return pick_aewa_batch(npt);
     }
     return nullptr;
+}
+
+void batch_start_items(const std::vector<double> &weight, int ctas, int *start) {
+    const int n = (int)weight.size();
+    double total = 0;
+    for (double w : weight) total += w;
+    int g = 0;
+    double below = 0;  // total weight of the items before g
+    for (int c = 0; c < ctas; ++c) {
+        // CTA c starts at the item holding weight position (c + 1/2) / ctas
+        const double pos = total > 0 ? (c + 0.5) / ctas * total : 0.0;
+        while (g < n - 1 && (weight[g] == 0 || below + weight[g] <= pos)) below += weight[g++];
+        start[c] = g;
+    }
 }
 
 namespace {
@@ -45,19 +58,17 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 extern "C" {
 
-size_t bpq_batch_workspace_bytes(int n_items, long total_shots, int tile_shots) {
-    if (n_items < 0 || total_shots < 0 || tile_shots < 1) return 0;
-    const long tiles = total_shots / tile_shots + n_items + 1;
-    return bpq::align256(bpq::kWorkspaceBytes) + bpq::align256(sizeof(bpq::DecodeArgs) * n_items) +
-           bpq::align256(sizeof(int4) * tiles);
+size_t bpq_batch_workspace_bytes(int n_items) {
+    if (n_items < 1) return 0;
+    return bpq::batch_counter_bytes(n_items) + bpq::align256(sizeof(bpq::DecodeArgs) * n_items) +
+           bpq::align256(sizeof(int) * bpq::kMaxBatchCtas);
 }
 
 int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const bpq_params *params, int max_iter,
-                   int tile_shots, void *work_dev, size_t work_bytes, void *stream, bpq_batch **out) {
+                   void *work_dev, size_t work_bytes, void *stream, bpq_batch **out) {
     if (!out) return fail(BPQ_EINVAL, "out is NULL");
     *out = nullptr;
     if (!items || n_items < 1) return fail(BPQ_EINVAL, "no batch items");
-    if (tile_shots < 1) return fail(BPQ_EINVAL, "tile_shots must be >= 1");
     if (max_iter < 1 || max_iter > 255) return fail(BPQ_EINVAL, "max_iter must be in [1, 255]");
     if (variant < BPQ_PLAIN || variant > BPQ_EWAINIT)
         return fail(BPQ_EINVAL, "the batched kernel takes plain, Momentum, AdaGrad or EWAInit BP");
@@ -67,22 +78,22 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
     for (int g = 0; g < n_items; ++g) {
         const bpq_tanner *t = items[g].tanner;
         if (!t || !t->dev_blob) return fail(BPQ_ESTATE, "batch item without an uploaded tanner");
-        if (t->device != device) return fail(BPQ_EINVAL, "batch items on different devices");
+        if (t->device != device) return fail(BPQ_ESTATE, "batch items on different devices");
         if (items[g].B < 0) return fail(BPQ_EINVAL, "negative shot count");
         if (items[g].B > 0 && (!items[g].syn_dev || !items[g].prior_dev || !items[g].est_dev ||
                                !items[g].conv_dev || !items[g].iters_dev))
             return fail(BPQ_EINVAL, "NULL input or output in a batch item");
         total += items[g].B;
     }
-    if (work_bytes < bpq_batch_workspace_bytes(n_items, total, tile_shots))
-        return fail(BPQ_EINVAL, "batch workspace too small");
+    if (work_bytes < bpq_batch_workspace_bytes(n_items)) return fail(BPQ_EINVAL, "batch workspace too small");
     int rc = bpq::cuda_set_device(device);
     if (rc) return rc;
 
     std::vector<bpq::DecodeArgs> desc(n_items);
-    std::vector<int4> tiles;
+    std::vector<double> weight(n_items);
     size_t smem = 0;
     int npt_max = 1;
+    long useful_ctas = 0;  // CTAs that the items can keep busy at once
     for (int g = 0; g < n_items; ++g) {
         const bpq_tanner *t = items[g].tanner;
         bpq::DecodeArgs &a = desc[g];
@@ -92,7 +103,6 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
         bpq::LaunchShape s;
         rc = bpq::decode_batch_shape(t, variant, &s);
         if (rc) return rc;
-        const int gpc = s.groups_per_cta;
         a.est = items[g].est_dev;
         a.conv = items[g].conv_dev;
         a.iters = items[g].iters_dev;
@@ -101,12 +111,11 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
         a.slots_floats = s.slots_floats;
         a.group_bytes = s.group_bytes;
         a.npt = s.npt;
-        a.groups_per_cta = gpc;
+        a.groups_per_cta = s.groups_per_cta;
         npt_max = std::max(npt_max, s.npt);
         smem = std::max(smem, s.smem);
-        const int per_tile = gpc * tile_shots;
-        for (int first = 0; first < items[g].B; first += per_tile)
-            tiles.push_back(make_int4(g, first, std::min(per_tile, items[g].B - first), 0));
+        weight[g] = (double)items[g].B * t->E;
+        useful_ctas += (items[g].B + s.groups_per_cta - 1) / s.groups_per_cta;
     }
     if (smem > 227 * 1024) return fail(BPQ_EINVAL, "a code of the batch needs more than 227 KB of shared memory");
 
@@ -117,19 +126,23 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bpq::kBatchThreads, smem);
     if (e != cudaSuccess || per_sm < 1) return fail(BPQ_ECUDA, "batched kernel does not fit on an SM");
+    long ctas = (long)per_sm * items[0].tanner->num_sms;
+    ctas = std::min<long>({ctas, std::max(1L, useful_ctas), (long)bpq::kMaxBatchCtas});
+    std::vector<int> start(ctas);
+    bpq::batch_start_items(weight, (int)ctas, start.data());
 
-    // device layout of the workspace: counters | descriptors | tiles
+    // device layout of the workspace: counters | descriptors | starting items
     uint8_t *w = static_cast<uint8_t *>(work_dev);
-    bpq::DecodeArgs *d_desc = reinterpret_cast<bpq::DecodeArgs *>(w + bpq::align256(bpq::kWorkspaceBytes));
-    int4 *d_tiles = reinterpret_cast<int4 *>(reinterpret_cast<uint8_t *>(d_desc) +
-                                             bpq::align256(sizeof(bpq::DecodeArgs) * n_items));
+    bpq::DecodeArgs *d_desc = reinterpret_cast<bpq::DecodeArgs *>(w + bpq::batch_counter_bytes(n_items));
+    int *d_start = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(d_desc) +
+                                           bpq::align256(sizeof(bpq::DecodeArgs) * n_items));
     for (auto &a : desc) a.work = static_cast<uint32_t *>(work_dev);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = bpq::cuda_check(cudaMemcpyAsync(d_desc, desc.data(), sizeof(bpq::DecodeArgs) * n_items,
                                          cudaMemcpyHostToDevice, st), "descriptor copy");
-    if (!rc && !tiles.empty())
-        rc = bpq::cuda_check(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(),
-                                             cudaMemcpyHostToDevice, st), "tile copy");
+    if (!rc)
+        rc = bpq::cuda_check(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice,
+                                             st), "start copy");
     if (!rc) rc = bpq::cuda_check(cudaStreamSynchronize(st), "plan sync");
     if (rc) return rc;
 
@@ -139,15 +152,13 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
     b->work = work_dev;
     b->fn = fn;
     b->args.codes = d_desc;
-    b->args.tiles = d_tiles;
-    b->args.ntiles = (int)tiles.size();
+    b->args.start = d_start;
+    b->args.ncodes = n_items;
     b->args.work = static_cast<uint32_t *>(work_dev);
     b->smem = smem;
     b->npt_max = npt_max;
     b->shots = total;
-    long ctas = (long)per_sm * items[0].tanner->num_sms;
-    if (ctas > b->args.ntiles) ctas = b->args.ntiles;
-    b->ctas = (int)std::max(1L, ctas);
+    b->ctas = (int)ctas;
     *out = b;
     return BPQ_OK;
 }
@@ -156,18 +167,19 @@ int bpq_batch_launch(const bpq_batch *b, void *stream) {
     if (!b) return fail(BPQ_EINVAL, "batch is NULL");
     int rc = bpq::cuda_set_device(b->device);
     if (rc) return rc;
-    if (b->args.ntiles == 0) return BPQ_OK;
+    if (b->shots == 0) return BPQ_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    rc = bpq::cuda_check(cudaMemsetAsync(b->work, 0, 8, st), "batch counter reset");
+    rc = bpq::cuda_check(cudaMemsetAsync(b->work, 0, bpq::batch_counter_bytes(b->args.ncodes), st),
+                         "batch counter reset");
     if (rc) return rc;
     b->fn<<<(unsigned)b->ctas, bpq::kBatchThreads, b->smem, st>>>(b->args);
     return bpq::cuda_check(cudaGetLastError(), "batched decode launch");
 }
 
-int bpq_batch_info(const bpq_batch *b, int *ctas, int *tiles, int *npt_max, long *shots) {
+int bpq_batch_info(const bpq_batch *b, int *ctas, int *items, int *npt_max, long *shots) {
     if (!b) return fail(BPQ_EINVAL, "batch is NULL");
     if (ctas) *ctas = b->ctas;
-    if (tiles) *tiles = b->args.ntiles;
+    if (items) *items = b->args.ncodes;
     if (npt_max) *npt_max = b->npt_max;
     if (shots) *shots = b->shots;
     return BPQ_OK;

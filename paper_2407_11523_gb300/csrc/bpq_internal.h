@@ -21,6 +21,19 @@ constexpr size_t kWorkspaceBytes = 256;  // [0] next shot, [1] device error word
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 
+// One qubit of the serial schedule's sweep (48 bytes, 16-byte aligned); the
+// serial table lists them level by level (see serial.cu).
+struct SerialVar {
+    uint16_t j;          // the qubit
+    uint8_t deg;         // its number of edges (<= 4)
+    uint8_t pauli;       // H_ij of edge k in bits 2k, 2k+1 (0 for k >= deg)
+    uint16_t own[4];     // check-major index of edge k (E, the zero slot, for k >= deg)
+    uint16_t chk[4];     // the check of edge k
+    uint16_t oth[4][3];  // the other edges of that check (E for padding)
+    uint16_t pad[2];
+};
+static_assert(sizeof(SerialVar) == 48, "SerialVar layout");
+
 }  // namespace bpq
 
 // Tanner graph handle.  Host fields are filled by the builders; device
@@ -46,6 +59,11 @@ struct bpq_tanner {
     bool split = false;
     std::vector<uint8_t> table_split;
     std::vector<int32_t> var_canon_split;  // 4 n4, indexed by split slot
+    // Serial schedule (bpq::build_serial_table): SerialVar[N] in level order |
+    // level_ptr u16[levels + 1] | chk_ptr u16[M + 1], padded to 16 bytes.
+    std::vector<uint8_t> serial;
+    int serial_levels = 0;
+    uint32_t serial_off_levels = 0, serial_off_chkptr = 0;
 
     // device
     int device = -1;
@@ -53,6 +71,7 @@ struct bpq_tanner {
     const uint8_t *d_table = nullptr;
     const int32_t *d_var_canon = nullptr;
     const uint8_t *d_table_split = nullptr;
+    const uint8_t *d_serial = nullptr;
     const int32_t *d_var_canon_split = nullptr;
     const int32_t *d_chk_ptr = nullptr;
     const uint8_t *d_logicals = nullptr;
@@ -65,4 +84,6 @@ struct bpq_tanner {
 namespace bpq {
 // Fill t->table, offsets and var_canon from the CSR; returns BPQ_OK or an error.
 int build_tables(bpq_tanner *t);
+// Fill t->serial (called by build_tables).
+int build_serial_table(bpq_tanner *t);
 }  // namespace bpq

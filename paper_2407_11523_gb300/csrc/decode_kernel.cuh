@@ -30,6 +30,12 @@
 //    and A without forming lambda (one reciprocal per edge, no logarithm).
 //  * message saturation: |m| <= msg_clip on both directions, i.e.
 //    delta(m_v->c) >= 2 / (e^msg_clip + 1) and |m_c->v| <= msg_clip.
+//  * units: every log-likelihood the kernel keeps (Pi, Q, S, the variant
+//    state and the c->v messages) is in bits, i.e. the paper's natural-log
+//    value times log2 e, so that ex2 and lg2 take and give them without a
+//    scale factor.  The decisions are unchanged (a positive scale), the EWA
+//    and momentum recursions are linear, AdaGrad's alpha and eps are scaled
+//    by log2 e on the host, and the trace reports natural-log values.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -160,9 +166,10 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // |w| = 2 atanh(1 - D) = ln((2 - D) / D).
 __device__ __forceinline__ float oplus(float a, float b) { return fmaf(-a, b, a + b); }
 
-// |m_{c->v}| = ln((2 - D) / D), D in [0, 1]; D = 0 (only certain incoming
-// messages, e.g. a degree-1 check) gives +inf, clipped by the caller.
-__device__ __forceinline__ float c2v_magnitude(float D) { return kLn2 * lg2((2.0f - D) * rcp(D)); }
+// |m_{c->v}| = log2((2 - D) / D) in bits (see the unit note at the top), D in
+// [0, 1]; D = 0 (only certain incoming messages, e.g. a degree-1 check) gives
+// +inf, clipped by the caller.
+__device__ __forceinline__ float c2v_magnitude(float D) { return lg2((2.0f - D) * rcp(D)); }
 
 // AdaGrad-BP keeps Gallager's form instead: v->c messages stored as
 // sign * phi(|m|), phi(x) = -ln tanh(x/2) (its own inverse), summed by the
@@ -176,18 +183,19 @@ struct PhiForm {
 };
 
 // Check-to-variable magnitude w = phi(S) = ln(1 + 2 / (e^S - 1)), S >= 0,
-// needed to an absolute accuracy.  e^S - 1 keeps its relative accuracy:
-// below S = 1/4 from its Taylor series to S^6/720 (truncation < 5e-8
-// relative), above from 2^(S log2 e) - 1 (the ex2 error is amplified at most
-// e^S/(e^S-1) < 4.6 times).  Then w = ln2 * lg2(1 + 2/(e^S-1)); S = 0 gives
-// w = inf (clipped by the caller), S -> inf gives w -> 0.
+// returned in bits (w log2 e), needed to an absolute accuracy.  e^S - 1
+// keeps its relative accuracy: below S = 1/4 from its Taylor series to
+// S^6/720 (truncation < 5e-8 relative), above from 2^(S log2 e) - 1 (the ex2
+// error is amplified at most e^S/(e^S-1) < 4.6 times).  Then
+// w log2 e = lg2(1 + 2/(e^S-1)); S = 0 gives inf (clipped by the caller),
+// S -> inf gives 0.
 __device__ __forceinline__ float phi_check(float S) {
     // (for S > 88, 2^(S log2 e) overflows to inf, 2/inf = 0 and w = 0)
     const float poly =
         S * fmaf(S, fmaf(S, fmaf(S, fmaf(S, fmaf(S, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f), 1.0f / 6.0f), 0.5f), 1.0f);
     const float big = ex2_always(S * kLog2e) - 1.0f;
     const float em1 = S < 0.25f ? poly : big;
-    return kLn2 * lg2(fmaf(2.0f, rcp(em1), 1.0f));
+    return lg2(fmaf(2.0f, rcp(em1), 1.0f));
 }
 
 // phi(|lambda|) = ln(1 + r), r = 2 min(C,A) / |C - A|, needed to a relative
@@ -249,8 +257,8 @@ template <bool TRACE, bool SPLIT, bool PHI, bool ALL>
 __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, float *slots, int j, int t, int shot, uint32_t vp,
                                          float QX, float QY, float QZ, const float (&win)[4], uint32_t ab) {
     const float c0 = fminf(0.f, fminf(QX, fminf(QY, QZ)));
-    const float e0 = ex2(c0 * kLog2e);
-    const float eX = ex2((c0 - QX) * kLog2e), eY = ex2((c0 - QY) * kLog2e), eZ = ex2((c0 - QZ) * kLog2e);
+    const float e0 = ex2(c0);
+    const float eX = ex2(c0 - QX), eY = ex2(c0 - QY), eZ = ex2(c0 - QZ);
     // C = 1 + e^{-Q_H} and the two anticommuting terms, for H = X, Y, Z
     const float CX = e0 + eX, CY = e0 + eY, CZ = e0 + eZ;
     const float AX = eY + eZ, AY = eX + eZ, AZ = eX + eY;
@@ -266,7 +274,7 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, float *slots, int 
             C = p == 1u ? CX : p == 2u ? CY : CZ;
             Ab = p == 1u ? AX : p == 2u ? AY : AZ;
         }
-        const float A = Ab * ex2(win[n] * kLog2e);
+        const float A = Ab * ex2(win[n]);
         // lambda = ln(C / A); delta = 1 - tanh(|lambda|/2) = 2 min(C, A) / (C + A),
         // at least delta_clip; or phi(|lambda|) = log1p(2 min(C, A) / |C - A|),
         // at least phi_clip (|lambda| <= msg_clip)
@@ -335,9 +343,9 @@ __device__ __forceinline__ void load_prior(const DecodeArgs &a, float *PiS) {
     for (int j = threadIdx.x; j < a.N; j += blockDim.x) {
         const float px = a.prior[3 * j], py = a.prior[3 * j + 1], pz = a.prior[3 * j + 2];
         const float pI = 1.0f - px - py - pz;
-        PiS[j] = logf(pI / px);
-        PiS[Np + j] = logf(pI / py);
-        PiS[2 * Np + j] = logf(pI / pz);
+        PiS[j] = log2f(pI / px);
+        PiS[Np + j] = log2f(pI / py);
+        PiS[2 * Np + j] = log2f(pI / pz);
     }
 }
 
@@ -451,11 +459,11 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
                         const float wv = fminf(PhiForm<VARIANT>::value ? phi_check(ext[n]) : c2v_magnitude(ext[n]),
-                                               a.clip);
+                                               a.clip2);
                         const float mm = __uint_as_float(__float_as_uint(wv) ^ ((sgn ^ u[n]) & 0x80000000u));
                         slots[sl[n] == kZero ? kTrash : sl[n]] = mm;
                         if (TRACE && a.tr_c2v && sl[n] != kZero)
-                            a.tr_c2v[((size_t)shot * a.max_iter + (t - 1)) * a.E + a.chk_ptr[i] + n] = mm;
+                            a.tr_c2v[((size_t)shot * a.max_iter + (t - 1)) * a.E + a.chk_ptr[i] + n] = kLn2 * mm;
                     }
                 }
             }
@@ -543,9 +551,9 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                 if (TRACE) {
                     const size_t o = (size_t)shot * a.max_iter + (t - 1);
                     if (a.tr_Q) {
-                        a.tr_Q[(o * N + j) * 3 + 0] = Q[0];
-                        a.tr_Q[(o * N + j) * 3 + 1] = Q[1];
-                        a.tr_Q[(o * N + j) * 3 + 2] = Q[2];
+                        a.tr_Q[(o * N + j) * 3 + 0] = kLn2 * Q[0];
+                        a.tr_Q[(o * N + j) * 3 + 1] = kLn2 * Q[1];
+                        a.tr_Q[(o * N + j) * 3 + 2] = kLn2 * Q[2];
                     }
                     if (a.tr_dec) a.tr_dec[o * N + j] = (uint8_t)d;
                 }
@@ -628,18 +636,19 @@ __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const 
     }
 }
 
-// Many codes in one launch.  Work comes in tiles (code g, first shot, count)
-// from a global queue ordered by code; a CTA of kBatchThreads splits into the
-// code's shot groups (T_g threads each), which take the tile's shots from a
-// shared counter.  When the code changes the CTA re-stages that code's
-// adjacency (bulk TMA) and prior.  Every shot is decoded by decode_shot, so
-// results equal those of decode_kernel bit for bit.
+// Many codes in one launch.  A CTA of kBatchThreads works on one item (a
+// code's batch) at a time: it splits into that code's shot groups (T_g
+// threads each), which take the item's shots one by one from the item's
+// global counter until none are left; only then does the CTA synchronise,
+// pick the next item with shots left (scanning from its starting item) and
+// re-stage that code's adjacency (bulk TMA) and prior.  Every shot is
+// decoded by decode_shot, so results equal those of decode_kernel bit for
+// bit.
 template <int VARIANT, int NPT>
 __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const BatchArgs b) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-    int *tile_slot = reinterpret_cast<int *>(smem + 8);    // current tile index
-    int *tile_ctr = reinterpret_cast<int *>(smem + 12);    // shots taken from the tile
+    int *code_slot = reinterpret_cast<int *>(smem + 8);    // the item being decoded
     int *grp_shot = reinterpret_cast<int *>(smem + 16);    // [kMaxGroupsPerCta]
     DecodeArgs *desc = reinterpret_cast<DecodeArgs *>(smem + kSmemHeader);
     uint8_t *tab = smem + kSmemHeader + kDescBytes;
@@ -648,21 +657,29 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
     if (tid == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
-        *tile_ctr = 0;
     }
     __syncthreads();
     int cur = -1;
+    int from = b.start[blockIdx.x < (unsigned)kMaxBatchCtas ? blockIdx.x : 0];
     uint32_t phase = 0;
     ThreadAdj<NPT> adj;
     for (;;) {
-        if (tid == 0) *tile_slot = (int)atomicAdd(b.work, 1u);
+        if (tid == 0) {
+            int pick = -1;
+            for (int k = 0; k < b.ncodes && pick < 0; ++k) {
+                const int g = (from + k) % b.ncodes;
+                const uint32_t taken = *reinterpret_cast<volatile const uint32_t *>(b.work + 2 + g);
+                if (taken < (uint32_t)b.codes[g].B) pick = g;
+            }
+            *code_slot = pick;
+        }
         __syncthreads();
-        const int tile = *tile_slot;
-        if (tile >= b.ntiles) break;
-        const int4 td = b.tiles[tile];  // (code, first shot, shot count, -)
-        if (td.x != cur) {
+        const int g = *code_slot;
+        if (g < 0) break;
+        from = g;
+        if (g != cur) {
             // switch code: descriptor, adjacency (bulk TMA), prior, zero slots
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(b.codes + td.x);
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(b.codes + g);
             for (int w = tid; w < (int)(sizeof(DecodeArgs) / 4); w += blockDim.x)
                 reinterpret_cast<uint32_t *>(desc)[w] = src[w];
             __syncthreads();
@@ -686,7 +703,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
             }
             load_adjacency<NPT>(*desc, tab, T, tid - group * T, desc->npt, adj);
             __syncthreads();
-            cur = td.x;
+            cur = g;
         }
         const DecodeArgs &a = *desc;
         const int G = a.G, T = G * 32;
@@ -695,18 +712,17 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
             const GroupMem m = group_mem(a, tab, group);
             const int bar_id = 1 + group;
             for (;;) {
-                if (tg == 0) grp_shot[group] = atomicAdd(tile_ctr, 1);
+                if (tg == 0) grp_shot[group] = (int)atomicAdd(b.work + 2 + g, 1u);
                 group_sync(G, bar_id);
-                const int k = grp_shot[group];
-                if (k >= td.z) break;
+                const int shot = grp_shot[group];
+                if (shot >= a.B) break;
                 if (a.split)
-                    decode_shot<VARIANT, NPT, false, true>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k, a.alpha);
+                    decode_shot<VARIANT, NPT, false, true>(a, adj, m, a.npt, T, tg, G, bar_id, shot, a.alpha);
                 else
-                    decode_shot<VARIANT, NPT, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, td.y + k, a.alpha);
+                    decode_shot<VARIANT, NPT, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, shot, a.alpha);
             }
         }
         __syncthreads();
-        if (tid == 0) *tile_ctr = 0;
     }
 }
 
@@ -727,8 +743,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
                                : dk::decode_kernel<BPQ_AEWA, 4, false, false>;           \
         }                                                                                \
         return nullptr;                                                                  \
-    }                                                                                    \
-    BatchKernelFn NAME##_batch(int) { return nullptr; }
+    }
 
 // Instantiate the kernels of one variant and return the one for (NPT,
 // trace, split layout).

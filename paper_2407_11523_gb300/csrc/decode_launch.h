@@ -4,11 +4,13 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "bpq_internal.h"
 
 namespace bpq {
 
-constexpr uint32_t kSmemHeader = 256;  // mbarrier, tile state, per-group shot indices
+constexpr uint32_t kSmemHeader = 256;  // mbarrier, current item, per-group shot indices
 constexpr int kMaxGroupsPerCta = 32;   // named barriers limit multi-warp groups to 15
 
 struct DecodeArgs {
@@ -27,6 +29,7 @@ struct DecodeArgs {
     int n_pad;                 // N rounded up to a multiple of 4 (shared-memory array stride)
     uint32_t slots_floats, group_bytes;
     float alpha, gamma, eps, clip, delta_clip, phi_clip;
+    float clip2;               // msg_clip in bits (msg_clip log2 e)
     int ada_from1;
     int split;                 // table in the split layout (bpq_tanner::split)
     // used by the batched kernel only
@@ -36,14 +39,20 @@ struct DecodeArgs {
 constexpr uint32_t kDescBytes = (sizeof(DecodeArgs) + 15) & ~15u;  // descriptor copy in shared memory
 constexpr int kBatchThreads = 1024;  // CTA size of the batched kernel
 
-// Arguments of the batched kernel: per-code descriptors and the tile list
-// (code, first shot, shot count), both in device memory.
+constexpr int kMaxBatchCtas = 1024;  // entries of the starting-item array
+
+// Arguments of the batched kernel, all in device memory: per-item
+// descriptors (B = the item's shots), each CTA's starting item, and the
+// counters work[1] (device error word) and work[2 + g] (next shot of item g).
 struct BatchArgs {
     const DecodeArgs *codes;
-    const int4 *tiles;
-    int ntiles;
-    uint32_t *work;  // [0] next tile, [1] device error word
+    const int *start;
+    int ncodes;
+    uint32_t *work;
 };
+
+// Bytes of the counter block of a batch of n items (zeroed before each run).
+inline size_t batch_counter_bytes(int n) { return ((size_t)4 * (2 + n) + 255) & ~size_t(255); }
 
 struct LaunchShape {
     int T, G, npt, groups_per_cta;
@@ -65,12 +74,15 @@ DecodeKernelFn pick_adagrad(int npt, bool trace, bool split);
 BatchKernelFn pick_adagrad_batch(int npt);
 DecodeKernelFn pick_ewainit(int npt, bool trace, bool split);
 DecodeKernelFn pick_aewa(int npt, bool trace, bool split);
-BatchKernelFn pick_aewa_batch(int npt);
 BatchKernelFn pick_ewainit_batch(int npt);
 
 int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
 // Shape of a code inside the batched kernel (CTAs of kBatchThreads threads).
 int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
+
+// Starting item of each of `ctas` CTAs, spread over the items in proportion
+// to weight[g] (shots x edges; items of weight 0 get none).
+void batch_start_items(const std::vector<double> &weight, int ctas, int *start);
 
 // Shared host helpers (api.cu).
 int need_uploaded(const bpq_tanner *t);

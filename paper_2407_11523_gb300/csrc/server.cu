@@ -37,12 +37,12 @@ struct Lane {
     // device slice
     uint32_t *work = nullptr;
     bpq::DecodeArgs *desc = nullptr;
-    int4 *tiles = nullptr;
+    int *start = nullptr;
     uint32_t *syn = nullptr;
     uint8_t *est = nullptr, *conv = nullptr, *iters = nullptr;
     // pinned host staging
     bpq::DecodeArgs *desc_h = nullptr;
-    int4 *tiles_h = nullptr;
+    int *start_h = nullptr;
     uint32_t *syn_h = nullptr;
     uint8_t *est_h = nullptr, *conv_h = nullptr, *iters_h = nullptr;
     // requests in flight: (request, code, offset of its estimate in est_h)
@@ -56,11 +56,10 @@ struct Lane {
 
 struct bpq_server {
     int device = -1;
-    int variant = 0, max_iter = 0, max_batch = 0, tile_shots = 0;
+    int variant = 0, max_iter = 0, max_batch = 0;
     std::vector<const bpq_tanner *> codes;
     std::vector<bpq::DecodeArgs> tmpl;  // per-code descriptor templates
-    std::vector<int> per_tile;          // shots per tile of each code
-    int Wmax = 0, Nmax = 0, max_tiles = 0;
+    int Wmax = 0, Nmax = 0;
     bpq::BatchKernelFn fn = nullptr;
     size_t smem = 0;
     int ctas = 0;
@@ -70,9 +69,10 @@ struct bpq_server {
 
 namespace {
 
-size_t lane_device_bytes(int n_codes, int max_batch, int max_tiles, int Wmax, int Nmax) {
-    return a256(bpq::kWorkspaceBytes) + a256(sizeof(bpq::DecodeArgs) * n_codes) + a256(sizeof(int4) * max_tiles) +
-           a256(sizeof(uint32_t) * (size_t)Wmax * max_batch) + a256((size_t)Nmax * max_batch) + 2 * a256(max_batch);
+size_t lane_device_bytes(int n_codes, int max_batch, int Wmax, int Nmax) {
+    return bpq::batch_counter_bytes(n_codes) + a256(sizeof(bpq::DecodeArgs) * n_codes) +
+           a256(sizeof(int) * bpq::kMaxBatchCtas) + a256(sizeof(uint32_t) * (size_t)Wmax * max_batch) +
+           a256((size_t)Nmax * max_batch) + 2 * a256(max_batch);
 }
 
 void free_server(bpq_server *s) {
@@ -83,7 +83,7 @@ void free_server(bpq_server *s) {
         if (l.done) cudaEventDestroy(l.done);
         if (l.st) cudaStreamDestroy(l.st);
         cudaFreeHost(l.desc_h);
-        cudaFreeHost(l.tiles_h);
+        cudaFreeHost(l.start_h);
         cudaFreeHost(l.syn_h);
         cudaFreeHost(l.est_h);
         cudaFreeHost(l.conv_h);
@@ -104,17 +104,16 @@ size_t bpq_server_device_bytes(const bpq_tanner *const *codes, int n_codes, int 
         Wmax = std::max(Wmax, (codes[c]->M + 31) / 32);
         Nmax = std::max(Nmax, codes[c]->N);
     }
-    return (size_t)n_lanes * lane_device_bytes(n_codes, max_batch, max_batch + n_codes, Wmax, Nmax);
+    return (size_t)n_lanes * lane_device_bytes(n_codes, max_batch, Wmax, Nmax);
 }
 
 int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors_dev, int n_codes, int variant,
-                      const bpq_params *params, int max_iter, int n_lanes, int max_batch, int tile_shots,
-                      void *dev_mem, size_t dev_bytes, bpq_server **out) {
+                      const bpq_params *params, int max_iter, int n_lanes, int max_batch, void *dev_mem,
+                      size_t dev_bytes, bpq_server **out) {
     if (!out) return fail(BPQ_EINVAL, "out is NULL");
     *out = nullptr;
     if (!codes || !priors_dev || n_codes < 1) return fail(BPQ_EINVAL, "no codes");
-    if (n_lanes < 1 || n_lanes > 64 || max_batch < 1 || tile_shots < 1)
-        return fail(BPQ_EINVAL, "bad lane count, batch size or tile size");
+    if (n_lanes < 1 || n_lanes > 64 || max_batch < 1) return fail(BPQ_EINVAL, "bad lane count or batch size");
     if (dev_bytes < bpq_server_device_bytes(codes, n_codes, n_lanes, max_batch) || !dev_mem)
         return fail(BPQ_EINVAL, "device memory budget too small");
     const int device = codes[0] ? codes[0]->device : -1;
@@ -124,7 +123,6 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
     s->variant = variant;
     s->max_iter = max_iter;
     s->max_batch = max_batch;
-    s->tile_shots = tile_shots;
     int rc = BPQ_OK;
     int npt_max = 1;
     for (int c = 0; c < n_codes && !rc; ++c) {
@@ -155,7 +153,6 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
         s->smem = std::max(s->smem, sh.smem);
         s->codes.push_back(t);
         s->tmpl.push_back(a);
-        s->per_tile.push_back(gpc * tile_shots);
         s->Wmax = std::max(s->Wmax, (t->M + 31) / 32);
         s->Nmax = std::max(s->Nmax, t->N);
     }
@@ -173,19 +170,18 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
         if (e != cudaSuccess || per_sm < 1) rc = fail(BPQ_ECUDA, "batched kernel does not fit on an SM");
         s->ctas = per_sm * s->codes[0]->num_sms;
     }
-    s->max_tiles = max_batch + n_codes;
-    const size_t lane_bytes = lane_device_bytes(n_codes, max_batch, s->max_tiles, s->Wmax, s->Nmax);
+    const size_t lane_bytes = lane_device_bytes(n_codes, max_batch, s->Wmax, s->Nmax);
     uint8_t *base = static_cast<uint8_t *>(dev_mem);
     for (int l = 0; l < n_lanes && !rc; ++l) {
         s->lanes.emplace_back();
         Lane &L = s->lanes.back();
         uint8_t *p = base + (size_t)l * lane_bytes;
         L.work = reinterpret_cast<uint32_t *>(p);
-        p += a256(bpq::kWorkspaceBytes);
+        p += bpq::batch_counter_bytes(n_codes);
         L.desc = reinterpret_cast<bpq::DecodeArgs *>(p);
         p += a256(sizeof(bpq::DecodeArgs) * n_codes);
-        L.tiles = reinterpret_cast<int4 *>(p);
-        p += a256(sizeof(int4) * s->max_tiles);
+        L.start = reinterpret_cast<int *>(p);
+        p += a256(sizeof(int) * bpq::kMaxBatchCtas);
         L.syn = reinterpret_cast<uint32_t *>(p);
         p += a256(sizeof(uint32_t) * (size_t)s->Wmax * max_batch);
         L.est = p;
@@ -196,7 +192,7 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
         cudaError_t e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaHostAlloc((void **)&L.desc_h, sizeof(bpq::DecodeArgs) * n_codes, 0);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&L.tiles_h, sizeof(int4) * s->max_tiles, 0);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&L.start_h, sizeof(int) * bpq::kMaxBatchCtas, 0);
         if (e == cudaSuccess) e = cudaHostAlloc((void **)&L.syn_h, sizeof(uint32_t) * (size_t)s->Wmax * max_batch, 0);
         if (e == cudaSuccess) e = cudaHostAlloc((void **)&L.est_h, (size_t)s->Nmax * max_batch, 0);
         if (e == cudaSuccess) e = cudaHostAlloc((void **)&L.conv_h, max_batch, 0);
@@ -288,8 +284,8 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
                 L.est_off.push_back(est_base[c] + (long)k * N);
                 L.shot_of.push_back(first[c] + k);
             }
-            int ntiles = 0;
-            int nd = 0;
+            std::vector<double> weight(n_codes);
+            long useful_ctas = 0;
             for (int c = 0; c < n_codes; ++c) {
                 bpq::DecodeArgs a = s->tmpl[c];
                 a.syn = L.syn + syn_base[c];
@@ -298,24 +294,26 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
                 a.iters = L.iters + first[c];
                 a.B = by_code_count[c];
                 a.work = L.work;
-                L.desc_h[nd] = a;
-                for (int f = 0; f < by_code_count[c]; f += s->per_tile[c])
-                    L.tiles_h[ntiles++] = make_int4(nd, f, std::min(s->per_tile[c], by_code_count[c] - f), 0);
-                ++nd;
+                L.desc_h[c] = a;
+                weight[c] = (double)by_code_count[c] * s->codes[c]->E;
+                useful_ctas += (by_code_count[c] + a.groups_per_cta - 1) / a.groups_per_cta;
             }
+            const int ctas = (int)std::min<long>({(long)s->ctas, std::max(1L, useful_ctas), (long)bpq::kMaxBatchCtas});
+            bpq::batch_start_items(weight, ctas, L.start_h);
             bpq::BatchArgs args;
             args.codes = L.desc;
-            args.tiles = L.tiles;
-            args.ntiles = ntiles;
+            args.start = L.start;
+            args.ncodes = n_codes;
             args.work = L.work;
             cudaError_t e = cudaMemcpyAsync(L.syn, L.syn_h, sizeof(uint32_t) * wsum, cudaMemcpyHostToDevice, L.st);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(L.desc, L.desc_h, sizeof(bpq::DecodeArgs) * nd, cudaMemcpyHostToDevice, L.st);
+                e = cudaMemcpyAsync(L.desc, L.desc_h, sizeof(bpq::DecodeArgs) * n_codes, cudaMemcpyHostToDevice,
+                                    L.st);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(L.tiles, L.tiles_h, sizeof(int4) * ntiles, cudaMemcpyHostToDevice, L.st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(L.work, 0, 8, L.st);
+                e = cudaMemcpyAsync(L.start, L.start_h, sizeof(int) * ctas, cudaMemcpyHostToDevice, L.st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(L.work, 0, bpq::batch_counter_bytes(n_codes), L.st);
             if (e == cudaSuccess) {
-                s->fn<<<(unsigned)std::min(s->ctas, ntiles), bpq::kBatchThreads, s->smem, L.st>>>(args);
+                s->fn<<<(unsigned)ctas, bpq::kBatchThreads, s->smem, L.st>>>(args);
                 e = cudaGetLastError();
                 ++s->launches;
             }

@@ -140,6 +140,70 @@ int build_tables(bpq_tanner *t) {
                 slot2[4 * i + n] = (uint16_t)slot_of_edge[e];
         std::memcpy(cp2, cp, (size_t)M_pad);
     }
+    return build_serial_table(t);
+}
+
+int build_serial_table(bpq_tanner *t) {
+    const int N = t->N, M = t->M, E = t->E;
+    if (E >= 0xFFFF || M >= 0xFFFF) return fail(BPQ_EINVAL, "code too large for the serial table");
+    // level(j) = 1 + the largest level among the earlier qubits sharing a check with j
+    std::vector<std::vector<int>> var_edges(N);
+    std::vector<int> edge_chk(E);
+    for (int i = 0; i < M; ++i)
+        for (int e = t->chk_ptr[i]; e < t->chk_ptr[i + 1]; ++e) {
+            var_edges[t->chk_var[e]].push_back(e);
+            edge_chk[e] = i;
+        }
+    std::vector<int> level(N), chk_last(M, -1);
+    int nlevels = 0;
+    for (int j = 0; j < N; ++j) {
+        int l = 0;
+        for (int e : var_edges[j]) l = std::max(l, chk_last[edge_chk[e]] + 1);
+        level[j] = l;
+        for (int e : var_edges[j]) chk_last[edge_chk[e]] = l;
+        nlevels = std::max(nlevels, l + 1);
+    }
+    std::vector<int> order(N);
+    for (int j = 0; j < N; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return level[x] < level[y]; });
+
+    const size_t vars_bytes = sizeof(SerialVar) * (size_t)N;
+    const size_t off_levels = vars_bytes;
+    const size_t off_chkptr = off_levels + 2 * (size_t)(nlevels + 1);
+    const size_t bytes = (off_chkptr + 2 * (size_t)(M + 1) + 15) & ~size_t(15);
+    t->serial.assign(bytes, 0);
+    SerialVar *vars = reinterpret_cast<SerialVar *>(t->serial.data());
+    uint16_t *lp = reinterpret_cast<uint16_t *>(t->serial.data() + off_levels);
+    uint16_t *cp = reinterpret_cast<uint16_t *>(t->serial.data() + off_chkptr);
+    for (int v = 0; v < N; ++v) {
+        const int j = order[v];
+        SerialVar &sv = vars[v];
+        sv.j = (uint16_t)j;
+        sv.deg = (uint8_t)var_edges[j].size();
+        sv.pauli = 0;
+        for (int k = 0; k < 4; ++k) {
+            sv.own[k] = (uint16_t)E;
+            sv.chk[k] = 0;
+            for (int f = 0; f < 3; ++f) sv.oth[k][f] = (uint16_t)E;
+        }
+        for (int k = 0; k < sv.deg; ++k) {
+            const int e = var_edges[j][k], i = edge_chk[e];
+            sv.own[k] = (uint16_t)e;
+            sv.chk[k] = (uint16_t)i;
+            sv.pauli |= (uint8_t)(t->chk_pauli[e] << (2 * k));
+            int f = 0;
+            for (int x = t->chk_ptr[i]; x < t->chk_ptr[i + 1]; ++x)
+                if (x != e) sv.oth[k][f++] = (uint16_t)x;
+        }
+    }
+    for (int l = 0, v = 0; l <= nlevels; ++l) {
+        while (v < N && level[order[v]] < l) ++v;
+        lp[l] = (uint16_t)v;
+    }
+    for (int i = 0; i <= M; ++i) cp[i] = (uint16_t)t->chk_ptr[i];
+    t->serial_levels = nlevels;
+    t->serial_off_levels = (uint32_t)off_levels;
+    t->serial_off_chkptr = (uint32_t)off_chkptr;
     return BPQ_OK;
 }
 

@@ -1,22 +1,30 @@
-// Differentiable unrolled EWAInit-BP (bpq_train_*): a fixed number T of
-// flooding iterations of EWAInit-BP (Sec. III-B, Algorithm 2) without the
-// stopping rule, with trainable per-iteration EWA weights alpha_t,
-// per-iteration damping beta_t of the variable-to-check messages and a
-// weight w_e on every check-to-variable message (neural-BP style; the paper's
-// conclusion names neural BP as a direction).  At alpha_t = alpha, beta_t = 0,
-// w_e = 1 the forward pass is EWAInit-BP.
+// Differentiable unrolled decoders (bpq_train_*): a fixed number T of
+// flooding iterations without the stopping rule, with per-iteration
+// trainable parameters, in two models:
 //
-//   Pi^(t)      = alpha_t Pi^(0) + (1 - alpha_t) Q^(t-1)              (t > 1)
+//   EWAInit (Sec. III-B, Algorithm 2), EWA weight alpha_t:
+//     Pi^(t)     = alpha_t Pi^(0) + (1 - alpha_t) Q^(t-1)              (t > 1)
+//     Q^(t)      = Pi^(t) + S^(t)
+//   Momentum (Sec. III-A1, eqs. (mombp1)-(mombp3)), step alpha_t, rate gamma_t:
+//     g^(t)      = gamma_t g^(t-1) + (1 - gamma_t) (Q^(t-1) - Pi^(0) - S^(t))
+//     Q^(t)      = Q^(t-1) - alpha_t g^(t),          Q^(0) = Pi^(0), g^(0) = 0
+//
+// and, in both, per-iteration damping beta_t of the variable-to-check
+// messages and a weight w_e on every check-to-variable message (neural-BP
+// style; the paper's conclusion names neural BP as a direction):
+//
 //   m_c->v^(t)  = clip(w_e (-1)^{s_i} r_e),  r_e = 2 atanh prod_{f != e} tanh(m_v->c^(t-1)_f / 2)
-//   Q^(t)       = Pi^(t) + sum of anticommuting m_c->v^(t)
+//   S^(t)       = sum of anticommuting m_c->v^(t)
 //   m_v->c^(t)  = (1 - beta_t) clip(lambda_H(Q^(t) - own message)) + beta_t m_v->c^(t-1)
 //   loss        = mean over shots and qubits of -log softmax(0, -Q_X, -Q_Y, -Q_Z)[true Pauli]
 //
-// One CTA decodes one shot (thread x owns check x and qubit x).  The forward
-// kernel stores a checkpoint (m_v->c, Q) every K iterations; the backward
-// kernel recomputes each K-iteration segment from its checkpoint into
-// shared memory and runs the adjoint through it in reverse.  The check-node
-// derivative uses d r_e / d m_f = sinh(r_e) / sinh(m_f), which follows from
+// At constant alpha (and gamma), beta_t = 0, w_e = 1 the forward pass is
+// EWAInit-BP (Momentum-BP).  One CTA decodes one shot (thread x owns check
+// x and qubit x).  The forward kernel stores a checkpoint (m_v->c, Q, and g
+// for Momentum) every K iterations; the backward kernel recomputes each
+// K-iteration segment from its checkpoint into shared memory and runs the
+// adjoint through it in reverse.  The check-node derivative uses
+// d r_e / d m_f = sinh(r_e) / sinh(m_f), which follows from
 // 1 - tanh^2 = 1 / cosh^2 and avoids the 1 / (1 - P^2) of the product form.
 // Per-shot gradient rows are reduced over shots by a separate kernel, so
 // results are deterministic.  Arithmetic is fp32 with accurate library
@@ -34,19 +42,23 @@ using bpq::fail;
 namespace bpq {
 namespace tr {
 
+constexpr int kEWAInit = BPQ_TRAIN_EWAINIT, kMomentum = BPQ_TRAIN_MOMENTUM;
+
 struct TrainArgs {
     const uint8_t *table;
     uint32_t off_chk_pauli, off_var_pauli;
     const int32_t *var_canon, *chk_ptr;
     const uint32_t *syn;
     const uint8_t *err;
-    const float *prior, *alpha, *beta, *w;
+    const float *prior, *alpha, *beta, *w, *gamma;
     int N, M, E, W, B, T, K, nck, n_pad;
+    int ck_floats;     // floats per checkpoint: 7 n_pad (EWAInit) or 10 n_pad (Momentum)
+    int width;         // floats per gradient row: 2T + E (+ T for Momentum)
     float clip;
-    float *ckpt;       // [B][nck][7 n_pad]: m_v->c (4 n_pad slots) then Q (3 n_pad)
+    float *ckpt;       // [B][nck][ck_floats]: m_v->c (4 n_pad slots), Q (3 n_pad), g (3 n_pad)
     float *loss_shot;  // [B] sum over qubits of the cross-entropy
     float *Q_out;      // optional [B][N][3]
-    float *rows;       // [B][2T + E] per-shot gradients
+    float *rows;       // [B][width] per-shot gradients: alpha | beta | w | gamma
 };
 
 __device__ __forceinline__ uint32_t anti(uint32_t a, uint32_t b) { return (a != 0u) & (b != 0u) & (a != b); }
@@ -136,6 +148,7 @@ __device__ __forceinline__ void check_forward(const TrainArgs &a, const Adj &d, 
 }
 
 // Forward: one CTA per shot.
+template <int MODEL>
 __global__ void train_forward_kernel(const TrainArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int Np = a.n_pad;
@@ -143,7 +156,8 @@ __global__ void train_forward_kernel(const TrainArgs a) {
     float *c2v = v2c + 4 * Np + 4;    // [4Np + 4]
     float *Pi0 = c2v + 4 * Np + 4;    // [3Np]
     float *Qp = Pi0 + 3 * Np;         // [3Np]
-    float *red = Qp + 3 * Np;         // [32]
+    float *Gp = Qp + 3 * Np;          // [3Np] momentum g^(t-1) (Momentum only)
+    float *red = Gp + (MODEL == kMomentum ? 3 * Np : 0);  // [32]
     const int x = threadIdx.x, shot = blockIdx.x;
     Adj d;
     load_adj(a, x, shot, d);
@@ -159,7 +173,10 @@ __global__ void train_forward_kernel(const TrainArgs a) {
         Pi0[x] = logf(pI / px);
         Pi0[Np + x] = logf(pI / py);
         Pi0[2 * Np + x] = logf(pI / pz);
-        for (int w = 0; w < 3; ++w) Qp[w * Np + x] = Pi0[w * Np + x];
+        for (int w = 0; w < 3; ++w) {
+            Qp[w * Np + x] = Pi0[w * Np + x];
+            if (MODEL == kMomentum) Gp[w * Np + x] = 0.f;
+        }
         // eq. (init)
         const float q[3] = {Pi0[x], Pi0[Np + x], Pi0[2 * Np + x]};
         for (int k = 0; k < 4; ++k) {
@@ -169,12 +186,14 @@ __global__ void train_forward_kernel(const TrainArgs a) {
         }
     }
     __syncthreads();
-    float *ck = a.ckpt + (size_t)shot * a.nck * 7 * Np;
+    float *ck = a.ckpt + (size_t)shot * a.nck * a.ck_floats;
     for (int t = 1; t <= a.T; ++t) {
-        if ((t - 1) % a.K == 0) {  // checkpoint (m_v->c^(t-1), Q^(t-1))
-            float *c = ck + (size_t)((t - 1) / a.K) * 7 * Np;
+        if ((t - 1) % a.K == 0) {  // checkpoint (m_v->c^(t-1), Q^(t-1), g^(t-1))
+            float *c = ck + (size_t)((t - 1) / a.K) * a.ck_floats;
             for (int k = x; k < 4 * Np; k += blockDim.x) c[k] = v2c[k];
             for (int k = x; k < 3 * Np; k += blockDim.x) c[4 * Np + k] = Qp[k];
+            if (MODEL == kMomentum)
+                for (int k = x; k < 3 * Np; k += blockDim.x) c[7 * Np + k] = Gp[k];
         }
         if (x < a.M) {
             float r[4], out[4];
@@ -192,8 +211,15 @@ __global__ void train_forward_kernel(const TrainArgs a) {
                 for (int w = 0; w < 3; ++w) S[w] += anti(w + 1, p) ? cin[k] : 0.f;
             }
             for (int w = 0; w < 3; ++w) {
-                const float pit = t > 1 ? al * Pi0[w * Np + x] + (1.f - al) * Qp[w * Np + x] : Pi0[w * Np + x];
-                Q[w] = pit + S[w];
+                if (MODEL == kMomentum) {
+                    const float gm = a.gamma[t - 1];
+                    const float g = gm * Gp[w * Np + x] + (1.f - gm) * (Qp[w * Np + x] - Pi0[w * Np + x] - S[w]);
+                    Q[w] = Qp[w * Np + x] - al * g;
+                    Gp[w * Np + x] = g;
+                } else {
+                    const float pit = t > 1 ? al * Pi0[w * Np + x] + (1.f - al) * Qp[w * Np + x] : Pi0[w * Np + x];
+                    Q[w] = pit + S[w];
+                }
             }
             for (int k = 0; k < 4; ++k) {
                 const uint32_t p = (d.vp >> (2 * k)) & 3u;
@@ -225,6 +251,7 @@ __global__ void train_forward_kernel(const TrainArgs a) {
 
 // Backward: one CTA per shot; segments of K iterations recomputed from the
 // checkpoints into shared memory, adjoint in reverse.
+template <int MODEL>
 __global__ void train_backward_kernel(const TrainArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int Np = a.n_pad, K = a.K, S4 = 4 * Np + 4;
@@ -232,7 +259,8 @@ __global__ void train_backward_kernel(const TrainArgs a) {
     float *vh = Pi0 + 3 * Np;                        // [(K+1)][S4]   m_v->c^(t0 .. t0+K)
     float *ch = vh + (size_t)(K + 1) * S4;           // [K][S4]       m_c->v^(t0+1 .. t0+K)
     float *Qh = ch + (size_t)K * S4;                 // [(K+1)][3Np]  Q^(t0 .. t0+K)
-    float *vbar = Qh + (size_t)(K + 1) * 3 * Np;     // [S4] adjoint of m_v->c^(t)
+    float *gh = Qh + (size_t)(K + 1) * 3 * Np;       // [(K+1)][3Np]  g^(t0 .. t0+K) (Momentum only)
+    float *vbar = gh + (MODEL == kMomentum ? (size_t)(K + 1) * 3 * Np : 0);  // [S4] adjoint of m_v->c^(t)
     float *cbar = vbar + S4;                         // [S4] adjoint of m_c->v^(t)
     float *red = cbar + S4;                          // [32]
     const int x = threadIdx.x, shot = blockIdx.x;
@@ -252,17 +280,20 @@ __global__ void train_backward_kernel(const TrainArgs a) {
         for (int s = 0; s < K; ++s) ch[(size_t)s * S4 + zero] = 0.f;
     }
     float Qbar[3] = {0.f, 0.f, 0.f};  // adjoint of Q^(t) of the owned qubit
+    float gbar[3] = {0.f, 0.f, 0.f};  // adjoint of g^(t) (Momentum)
     float wbar[4] = {0.f, 0.f, 0.f, 0.f};
-    float *row = a.rows + (size_t)shot * (2 * a.T + a.E);
+    float *row = a.rows + (size_t)shot * a.width;
     const float sigma = d.sb ? -1.f : 1.f;
     __syncthreads();
 
     for (int c = a.nck - 1; c >= 0; --c) {
         const int t0 = c * K, t1 = min(a.T, t0 + K);
         // ---- recompute iterations t0+1 .. t1 from checkpoint c ----
-        const float *ck = a.ckpt + ((size_t)shot * a.nck + c) * 7 * Np;
+        const float *ck = a.ckpt + ((size_t)shot * a.nck + c) * a.ck_floats;
         for (int k = x; k < 4 * Np; k += blockDim.x) vh[k] = ck[k];
         for (int k = x; k < 3 * Np; k += blockDim.x) Qh[k] = ck[4 * Np + k];
+        if (MODEL == kMomentum)
+            for (int k = x; k < 3 * Np; k += blockDim.x) gh[k] = ck[7 * Np + k];
         __syncthreads();
         for (int t = t0 + 1; t <= t1; ++t) {
             const int s = t - t0;
@@ -287,8 +318,18 @@ __global__ void train_backward_kernel(const TrainArgs a) {
                     for (int w = 0; w < 3; ++w) Sm[w] += anti(w + 1, p) ? cin[k] : 0.f;
                 }
                 for (int w = 0; w < 3; ++w) {
-                    const float pit = t > 1 ? al * Pi0[w * Np + x] + (1.f - al) * Qprev[w * Np + x] : Pi0[w * Np + x];
-                    Q[w] = pit + Sm[w];
+                    if (MODEL == kMomentum) {
+                        const float gm = a.gamma[t - 1];
+                        const float *gprev = gh + (size_t)(s - 1) * 3 * Np;
+                        const float g = gm * gprev[w * Np + x] +
+                                        (1.f - gm) * (Qprev[w * Np + x] - Pi0[w * Np + x] - Sm[w]);
+                        Q[w] = Qprev[w * Np + x] - al * g;
+                        gh[(size_t)s * 3 * Np + w * Np + x] = g;
+                    } else {
+                        const float pit =
+                            t > 1 ? al * Pi0[w * Np + x] + (1.f - al) * Qprev[w * Np + x] : Pi0[w * Np + x];
+                        Q[w] = pit + Sm[w];
+                    }
                     Qnew[w * Np + x] = Q[w];
                 }
                 for (int k = 0; k < 4; ++k) {
@@ -327,7 +368,7 @@ __global__ void train_backward_kernel(const TrainArgs a) {
             const float *Qt = Qh + (size_t)s * 3 * Np;        // Q^(t)
             const float *Qprev = Qh + (size_t)(s - 1) * 3 * Np;
             const float al = a.alpha[t - 1], be = a.beta[t - 1];
-            float bb = 0.f, ab = 0.f;
+            float bb = 0.f, ab = 0.f, gb = 0.f;
             // step A (qubit role): damping, lambda, posterior, EWA prior
             if (x < a.N) {
                 float Qacc[3] = {0.f, 0.f, 0.f}, cb_part[4] = {0.f, 0.f, 0.f, 0.f};
@@ -351,30 +392,55 @@ __global__ void train_backward_kernel(const TrainArgs a) {
                         }
                     }
                 }
-                float Qtot[3];
+                float Qtot[3], Sbar[3];
                 for (int w = 0; w < 3; ++w) Qtot[w] = Qbar[w] + Qacc[w];
+                if (MODEL == kMomentum) {
+                    // Q^(t) = Q^(t-1) - alpha g^(t);  g^(t) = gamma g^(t-1) + (1 - gamma) D,
+                    // D = Q^(t-1) - Pi^(0) - S^(t)
+                    const float gm = a.gamma[t - 1];
+                    const float *gt = gh + (size_t)s * 3 * Np, *gprev = gh + (size_t)(s - 1) * 3 * Np;
+                    float Sm[3] = {0.f, 0.f, 0.f};
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t p = (d.vp >> (2 * k)) & 3u;
+                        for (int w = 0; w < 3; ++w)
+                            if (p && anti(w + 1, p)) Sm[w] += c_t[4 * x + k];
+                    }
+                    for (int w = 0; w < 3; ++w) {
+                        const float gtot = gbar[w] - al * Qtot[w];  // adjoint of g^(t)
+                        const float D = Qprev[w * Np + x] - Pi0[w * Np + x] - Sm[w];
+                        ab -= Qtot[w] * gt[w * Np + x];
+                        gb += gtot * (gprev[w * Np + x] - D);
+                        Sbar[w] = -(1.f - gm) * gtot;
+                        Qbar[w] = Qtot[w] + (1.f - gm) * gtot;  // adjoint of Q^(t-1)
+                        gbar[w] = gm * gtot;                    // adjoint of g^(t-1)
+                    }
+                } else {
+                    for (int w = 0; w < 3; ++w) Sbar[w] = Qtot[w];
+                    if (t > 1) {
+                        for (int w = 0; w < 3; ++w) {
+                            ab += Qtot[w] * (Pi0[w * Np + x] - Qprev[w * Np + x]);
+                            Qbar[w] = (1.f - al) * Qtot[w];
+                        }
+                    } else {
+                        Qbar[0] = Qbar[1] = Qbar[2] = 0.f;
+                    }
+                }
                 for (int k = 0; k < 4; ++k) {
                     const uint32_t p = (d.vp >> (2 * k)) & 3u;
                     float cb = cb_part[k];
                     for (int w = 0; w < 3; ++w)
-                        if (anti(w + 1, p)) cb += Qtot[w];
+                        if (anti(w + 1, p)) cb += Sbar[w];
                     cbar[4 * x + k] = p ? cb : 0.f;
                     vbar[4 * x + k] = p ? be * vbar[4 * x + k] : 0.f;  // damping path to m_v->c^(t-1)
-                }
-                if (t > 1) {
-                    for (int w = 0; w < 3; ++w) {
-                        ab += Qtot[w] * (Pi0[w * Np + x] - Qprev[w * Np + x]);
-                        Qbar[w] = (1.f - al) * Qtot[w];
-                    }
-                } else {
-                    Qbar[0] = Qbar[1] = Qbar[2] = 0.f;
                 }
             }
             const float sum_b = block_sum(bb, red);
             const float sum_a = block_sum(ab, red);
+            const float sum_g = MODEL == kMomentum ? block_sum(gb, red) : 0.f;
             if (x == 0) {
-                row[t - 1] = t > 1 ? sum_a : 0.f;
+                row[t - 1] = (MODEL == kMomentum || t > 1) ? sum_a : 0.f;
                 row[a.T + t - 1] = sum_b;
+                if (MODEL == kMomentum) row[2 * a.T + a.E + t - 1] = sum_g;
             }
             __syncthreads();
             // step B (check role): message weights and the check-node derivative
@@ -434,16 +500,19 @@ __global__ void reduce_rows_kernel(const float *rows, int B, int width, int offs
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int fill(const bpq_tanner *t, const uint32_t *syn, const uint8_t *err, const float *prior, int B, int T, int K,
-         const float *alpha, const float *beta, const float *w, float clip, void *work, size_t work_bytes,
-         TrainArgs &a) {
+int fill(const bpq_tanner *t, int model, const uint32_t *syn, const uint8_t *err, const float *prior, int B, int T,
+         int K, const float *alpha, const float *beta, const float *gamma, const float *w, float clip, void *work,
+         size_t work_bytes, TrainArgs &a) {
     int rc = need_uploaded(t);
     if (rc) return rc;
+    if (model != kEWAInit && model != kMomentum) return fail(BPQ_EINVAL, "unknown training model");
     if (B < 1 || T < 1 || T > 255 || K < 1) return fail(BPQ_EINVAL, "bad B, T or checkpoint interval");
     if (!syn || !err || !prior || !alpha || !beta || !w || !work) return fail(BPQ_EINVAL, "NULL argument");
+    if (model == kMomentum && !gamma) return fail(BPQ_EINVAL, "the Momentum model needs gamma");
     if (!(clip > 0.f)) return fail(BPQ_EINVAL, "msg_clip must be positive");
     if (std::max(t->N, t->M) > 1024) return fail(BPQ_EINVAL, "training kernels take codes of up to 1024 nodes");
-    if (work_bytes < bpq_train_workspace_bytes(t, B, T, K)) return fail(BPQ_EINVAL, "training workspace too small");
+    if (work_bytes < bpq_train_workspace_bytes(t, model, B, T, K))
+        return fail(BPQ_EINVAL, "training workspace too small");
     a = TrainArgs{};
     a.table = t->d_table;
     a.off_chk_pauli = t->off_chk_pauli;
@@ -456,6 +525,7 @@ int fill(const bpq_tanner *t, const uint32_t *syn, const uint8_t *err, const flo
     a.alpha = alpha;
     a.beta = beta;
     a.w = w;
+    a.gamma = gamma;
     a.N = t->N;
     a.M = t->M;
     a.E = t->E;
@@ -465,10 +535,12 @@ int fill(const bpq_tanner *t, const uint32_t *syn, const uint8_t *err, const flo
     a.K = K;
     a.nck = (T + K - 1) / K;
     a.n_pad = (t->N + 3) & ~3;
+    a.ck_floats = (model == kMomentum ? 10 : 7) * a.n_pad;
+    a.width = (model == kMomentum ? 3 : 2) * T + t->E;
     a.clip = clip;
     uint8_t *p = static_cast<uint8_t *>(work);
     a.ckpt = reinterpret_cast<float *>(p);
-    p += a256(sizeof(float) * (size_t)B * a.nck * 7 * a.n_pad);
+    p += a256(sizeof(float) * (size_t)B * a.nck * a.ck_floats);
     a.loss_shot = reinterpret_cast<float *>(p);
     p += a256(sizeof(float) * B);
     a.rows = reinterpret_cast<float *>(p);
@@ -482,57 +554,71 @@ int threads_for(const bpq_tanner *t) { return ((std::max(t->N, t->M) + 31) / 32)
 
 extern "C" {
 
-size_t bpq_train_workspace_bytes(const bpq_tanner *t, int B, int T, int ckpt_every) {
+size_t bpq_train_workspace_bytes(const bpq_tanner *t, int model, int B, int T, int ckpt_every) {
     if (!t || B < 1 || T < 1 || ckpt_every < 1) return 0;
+    if (model != BPQ_TRAIN_EWAINIT && model != BPQ_TRAIN_MOMENTUM) return 0;
     const size_t np = (size_t)((t->N + 3) & ~3);
     const size_t nck = (size_t)((T + ckpt_every - 1) / ckpt_every);
-    return bpq::tr::a256(sizeof(float) * (size_t)B * nck * 7 * np) + bpq::tr::a256(sizeof(float) * B) +
-           bpq::tr::a256(sizeof(float) * (size_t)B * (2 * T + t->E));
+    const size_t per_ck = (model == BPQ_TRAIN_MOMENTUM ? 10 : 7) * np;
+    const size_t width = (size_t)(model == BPQ_TRAIN_MOMENTUM ? 3 : 2) * T + t->E;
+    return bpq::tr::a256(sizeof(float) * (size_t)B * nck * per_ck) + bpq::tr::a256(sizeof(float) * B) +
+           bpq::tr::a256(sizeof(float) * (size_t)B * width);
 }
 
-int bpq_train_forward(const bpq_tanner *t, const uint32_t *syn_dev, const uint8_t *err_dev, const float *prior_dev,
-                      int B, int T, int ckpt_every, const float *alpha_dev, const float *beta_dev, const float *w_dev,
-                      float msg_clip, float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes, void *stream) {
+int bpq_train_forward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
+                      const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
+                      const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
+                      float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes, void *stream) {
     bpq::tr::TrainArgs a;
-    int rc = bpq::tr::fill(t, syn_dev, err_dev, prior_dev, B, T, ckpt_every, alpha_dev, beta_dev, w_dev, msg_clip,
-                           work_dev, work_bytes, a);
+    int rc = bpq::tr::fill(t, model, syn_dev, err_dev, prior_dev, B, T, ckpt_every, alpha_dev, beta_dev, gamma_dev,
+                           w_dev, msg_clip, work_dev, work_bytes, a);
     if (rc) return rc;
     if (!loss_dev) return fail(BPQ_EINVAL, "NULL loss output");
     a.Q_out = Q_dev;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t smem = sizeof(float) * (2 * (4 * a.n_pad + 4) + 6 * a.n_pad + 32);
-    cudaError_t e = cudaFuncSetAttribute(bpq::tr::train_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const bool mom = model == BPQ_TRAIN_MOMENTUM;
+    const size_t smem = sizeof(float) * (2 * (4 * a.n_pad + 4) + (mom ? 9 : 6) * a.n_pad + 32);
+    void (*fn)(const bpq::tr::TrainArgs) = mom ? bpq::tr::train_forward_kernel<bpq::tr::kMomentum>
+                                               : bpq::tr::train_forward_kernel<bpq::tr::kEWAInit>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("train forward attribute: ") + cudaGetErrorString(e));
-    bpq::tr::train_forward_kernel<<<B, bpq::tr::threads_for(t), smem, st>>>(a);
+    fn<<<B, bpq::tr::threads_for(t), smem, st>>>(a);
     bpq::tr::reduce_rows_kernel<<<1, 32, 0, st>>>(a.loss_shot, B, 1, 0, 1, loss_dev, 1.f / ((float)B * (float)t->N));
     return bpq::cuda_check(cudaGetLastError(), "train forward launch");
 }
 
-int bpq_train_backward(const bpq_tanner *t, const uint32_t *syn_dev, const uint8_t *err_dev, const float *prior_dev,
-                       int B, int T, int ckpt_every, const float *alpha_dev, const float *beta_dev, const float *w_dev,
-                       float msg_clip, float *grad_alpha_dev, float *grad_beta_dev, float *grad_w_dev, void *work_dev,
-                       size_t work_bytes, void *stream) {
+int bpq_train_backward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
+                       const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
+                       const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
+                       float *grad_alpha_dev, float *grad_beta_dev, float *grad_gamma_dev, float *grad_w_dev,
+                       void *work_dev, size_t work_bytes, void *stream) {
     bpq::tr::TrainArgs a;
-    int rc = bpq::tr::fill(t, syn_dev, err_dev, prior_dev, B, T, ckpt_every, alpha_dev, beta_dev, w_dev, msg_clip,
-                           work_dev, work_bytes, a);
+    int rc = bpq::tr::fill(t, model, syn_dev, err_dev, prior_dev, B, T, ckpt_every, alpha_dev, beta_dev, gamma_dev,
+                           w_dev, msg_clip, work_dev, work_bytes, a);
     if (rc) return rc;
-    if (!grad_alpha_dev || !grad_beta_dev || !grad_w_dev) return fail(BPQ_EINVAL, "NULL gradient output");
+    const bool mom = model == BPQ_TRAIN_MOMENTUM;
+    if (!grad_alpha_dev || !grad_beta_dev || !grad_w_dev || (mom && !grad_gamma_dev))
+        return fail(BPQ_EINVAL, "NULL gradient output");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int K = a.K, Np = a.n_pad, S4 = 4 * Np + 4;
-    const size_t smem = sizeof(float) * (3 * Np + (size_t)(K + 1) * S4 + (size_t)K * S4 + (size_t)(K + 1) * 3 * Np +
-                                         2 * S4 + 32);
+    const size_t hist = (size_t)(K + 1) * 3 * Np * (mom ? 2 : 1);
+    const size_t smem =
+        sizeof(float) * (3 * Np + (size_t)(K + 1) * S4 + (size_t)K * S4 + hist + 2 * S4 + 32);
     if (smem > 227 * 1024) return fail(BPQ_EINVAL, "checkpoint interval too long for shared memory");
-    cudaError_t e = cudaFuncSetAttribute(bpq::tr::train_backward_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void (*fn)(const bpq::tr::TrainArgs) = mom ? bpq::tr::train_backward_kernel<bpq::tr::kMomentum>
+                                               : bpq::tr::train_backward_kernel<bpq::tr::kEWAInit>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("train backward attribute: ") + cudaGetErrorString(e));
-    bpq::tr::train_backward_kernel<<<B, bpq::tr::threads_for(t), smem, st>>>(a);
-    // per-shot rows hold [alpha | beta | w]
-    const int width = 2 * T + t->E;
+    fn<<<B, bpq::tr::threads_for(t), smem, st>>>(a);
+    // per-shot rows hold [alpha | beta | w | gamma]
+    const int width = a.width;
     bpq::tr::reduce_rows_kernel<<<(T + 127) / 128, 128, 0, st>>>(a.rows, B, width, 0, T, grad_alpha_dev, 1.f);
     bpq::tr::reduce_rows_kernel<<<(T + 127) / 128, 128, 0, st>>>(a.rows, B, width, T, T, grad_beta_dev, 1.f);
     bpq::tr::reduce_rows_kernel<<<(t->E + 127) / 128, 128, 0, st>>>(a.rows, B, width, 2 * T, t->E, grad_w_dev,
                                                                      1.f);
+    if (mom)
+        bpq::tr::reduce_rows_kernel<<<(T + 127) / 128, 128, 0, st>>>(a.rows, B, width, 2 * T + t->E, T,
+                                                                     grad_gamma_dev, 1.f);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("train backward launch: ") + cudaGetErrorString(e));
     return BPQ_OK;

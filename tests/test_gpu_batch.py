@@ -37,7 +37,7 @@ def build_items(bpq, sizes, seed=100):
 def test_batched_equals_per_code_decode(bpq, variant):
     sizes = [3000, 1700, 2500, 0, 257, 900, 1200, 31]   # uneven, with an empty and a ragged item
     items = build_items(bpq, sizes)
-    plan = bpq.BatchPlan(items, variant=variant, max_iter=100, tile_shots=16)
+    plan = bpq.BatchPlan(items, variant=variant, max_iter=100)
     outs = plan.run()
     for (t, syn, prior), got in zip(items, outs):
         ref = bpq.decode(t, syn, prior, variant, max_iter=100)
@@ -126,7 +126,7 @@ def test_batched_mixed_layouts(bpq, variant):
     for k, t in enumerate(codes):
         _, syn = bpq.sample(t, *ch, seed=400 + k, shot0=0, B=700 + 37 * k)
         items.append((t, syn, bpq.prior_tensor(t, *ch)))
-    plan = bpq.BatchPlan(items, variant=variant, max_iter=60, tile_shots=16)
+    plan = bpq.BatchPlan(items, variant=variant, max_iter=60)
     outs = plan.run()
     for (t, syn, prior), got in zip(items, outs):
         ref = bpq.decode(t, syn, prior, variant, max_iter=60)

@@ -124,3 +124,68 @@ def test_training_lowers_the_loss(bpq):
             b.clamp_(0.0, 0.95)
         losses.append(float(L))
     assert losses[-1] < losses[0]
+
+
+def test_momentum_model_at_fixed_parameters_is_momentum_bp(bpq):
+    """The Momentum model at constant alpha, gamma, beta = 0, w = 1 is
+    Momentum-BP (eqs. (mombp1), (mombp2), (mombp5)): its final posterior
+    matches the C oracle's Momentum-BP trace."""
+    t, err, syn, prior, ch = setup(bpq, 16, 0.05, 11, d=7)
+    T = 10
+    Q, _ = bpq.unrolled_posterior(t, syn, err, prior, torch.full((T,), 0.6, device="cuda"),
+                                  torch.zeros(T, device="cuda"), torch.ones(t.E, device="cuda"), T=T,
+                                  model="momentum", gamma=torch.full((T,), 0.3, device="cuda"))
+    H, s, e, pri = oracle_inputs(t, err, syn, ch)
+    Q = Q.cpu().numpy()
+    for b in range(s.shape[0]):
+        tr = oracle.trace(H, s[b], pri, variant="momentum", alpha=0.6, gamma=0.3, T=T)
+        assert np.abs(Q[b] - tr["Q"][-1]).max() <= 4e-4 + 1e-5 * np.abs(tr["Q"][-1]).max()
+
+
+@pytest.mark.parametrize("T", [6, 12])
+def test_momentum_gradients_match_oracle_and_finite_differences(bpq, T):
+    t, err, syn, prior, ch = setup(bpq, 8, 0.06, 13)
+    rng = np.random.default_rng(14)
+    a = 0.6 + 0.1 * rng.standard_normal(T)
+    gm = 0.3 + 0.1 * rng.standard_normal(T)
+    b = 0.1 * np.abs(rng.standard_normal(T))
+    w = 1.0 + 0.1 * rng.standard_normal(t.E)
+    ts = [torch.tensor(x, device="cuda", dtype=torch.float32, requires_grad=True) for x in (a, b, w, gm)]
+    L = bpq.unrolled_loss(t, syn, err, prior, ts[0], ts[1], ts[2], T=T, ckpt_every=5, model="momentum",
+                          gamma=ts[3])
+    L.backward()
+    ga, gb, gw, gg = (x.grad.detach().cpu().numpy().astype(np.float64) for x in ts)
+    H, s, e, pri = oracle_inputs(t, err, syn, ch)
+    Lr, ra, rb, rw, rg = unrolled.loss_and_grads(H, s, e, pri, a, b, w, T, model="momentum", gamma=gm)
+    assert float(L) == pytest.approx(Lr, rel=2e-4)
+    for g, r in ((ga, ra), (gb, rb), (gw, rw), (gg, rg)):
+        scale = np.abs(r).max()
+        assert np.abs(g - r).max() <= 2e-3 * scale + 1e-7, (np.abs(g - r).max(), scale)
+    g = unrolled.Graph(H)
+
+    def f(aa, gg_):
+        return float(unrolled.loss(unrolled.forward(g, s, pri, torch.tensor(aa), torch.tensor(b), torch.tensor(w), T,
+                                                    model="momentum", gamma=torch.tensor(gg_)), e))
+
+    h = 1e-6
+    for k in (0, T - 1):
+        dv = np.zeros(T); dv[k] = h
+        assert ga[k] == pytest.approx((f(a + dv, gm) - f(a - dv, gm)) / (2 * h), rel=5e-3, abs=1e-6)
+        assert gg[k] == pytest.approx((f(a, gm + dv) - f(a, gm - dv)) / (2 * h), rel=5e-3, abs=1e-6)
+
+
+def test_momentum_backward_is_checkpoint_independent(bpq):
+    t, err, syn, prior, ch = setup(bpq, 32, 0.07, 15)
+    T = 20
+    rng = np.random.default_rng(16)
+    vals = (0.6 + 0.05 * rng.standard_normal(T), 0.05 * np.abs(rng.standard_normal(T)),
+            1.0 + 0.05 * rng.standard_normal(t.E), 0.3 + 0.05 * rng.standard_normal(T))
+    grads = []
+    for K in (5, 20, 7):
+        ts = [torch.tensor(x, device="cuda", dtype=torch.float32, requires_grad=True) for x in vals]
+        bpq.unrolled_loss(t, syn, err, prior, ts[0], ts[1], ts[2], T=T, ckpt_every=K, model="momentum",
+                          gamma=ts[3]).backward()
+        grads.append([x.grad.clone() for x in ts])
+    for gk in grads[1:]:
+        for g0, g1 in zip(grads[0], gk):
+            assert torch.equal(g0, g1)
