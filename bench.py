@@ -627,7 +627,7 @@ def run_serial(args, rank, world):
 
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    B = SERIAL_SHOTS
+    B = min(SERIAL_SHOTS, args.shots_per_p)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     work = bpq.workspace(dev)
     rows, timed_ms, launches = [], 0.0, 0
