@@ -267,6 +267,113 @@ int cuda_set_device(int device) {
     return BPQ_OK;
 }
 
+// Copy streams of one device for the pipelined host path (created on first
+// use, kept for the life of the process).
+struct HostPipe {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+};
+std::mutex g_pipe_mu;
+HostPipe g_pipe[64];
+
+int host_pipe(int device, HostPipe **out) {
+    if (device < 0 || device >= 64) return fail(BPQ_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_pipe_mu);
+    HostPipe &hp = g_pipe[device];
+    if (!hp.h2d) {
+        int rc = cuda_check(cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking), "copy stream");
+        if (rc) return rc;
+        rc = cuda_check(cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking), "copy stream");
+        if (rc) return rc;
+    }
+    *out = &hp;
+    return BPQ_OK;
+}
+
+// bpq_decode_host.  With `pipelined`, batches of at least 2 x kChunkShots
+// shots are cut into up to kMaxChunks chunks whose host-to-device copies
+// (one copy stream), decodes (the caller's stream) and device-to-host copies
+// (a second copy stream) overlap, ordered by events; without it (the
+// no-allocation path) everything runs on the caller's stream in order.
+int decode_host_impl(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
+                     const bpq_params *params, int max_iter, int B, uint8_t *est_host, uint8_t *conv_host,
+                     uint8_t *iters_host, void *dev_buf, size_t dev_buf_bytes, void *stream, bool pipelined) {
+    constexpr int kChunkShots = 1 << 16, kMaxChunks = 8;
+    int rc = need_uploaded(t);
+    if (rc) return rc;
+    if (B < 0) return fail(BPQ_EINVAL, "B < 0");
+    if (B == 0) return BPQ_OK;
+    if (!syn_host || !prior_host || !est_host || !conv_host || !iters_host || !dev_buf)
+        return fail(BPQ_EINVAL, "NULL argument");
+    if (dev_buf_bytes < bpq_decode_host_bytes(t, B)) return fail(BPQ_EINVAL, "device buffer too small");
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t W = (t->M + 31) / 32, N = (size_t)t->N;
+    uint8_t *p = static_cast<uint8_t *>(dev_buf);
+    void *work = p;
+    p += al(kWorkspaceBytes);
+    uint32_t *syn = reinterpret_cast<uint32_t *>(p);
+    p += al(sizeof(uint32_t) * W * B);
+    float *prior = reinterpret_cast<float *>(p);
+    p += al(sizeof(float) * 3 * t->N);
+    uint8_t *est = p;
+    p += al((size_t)B * N);
+    uint8_t *conv = p;
+    p += al(B);
+    uint8_t *iters = p;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int chunks = pipelined ? std::min(kMaxChunks, B / kChunkShots) : 1;
+    if (chunks < 2) {
+        rc = cuda_check(cudaMemcpyAsync(syn, syn_host, sizeof(uint32_t) * W * B, cudaMemcpyHostToDevice, st), "H2D");
+        if (!rc)
+            rc = cuda_check(cudaMemcpyAsync(prior, prior_host, sizeof(float) * 3 * t->N, cudaMemcpyHostToDevice, st),
+                            "H2D");
+        if (!rc) rc = bpq_decode(t, syn, prior, variant, params, max_iter, B, est, conv, iters, work, stream);
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(est_host, est, (size_t)B * N, cudaMemcpyDeviceToHost, st), "D2H");
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(conv_host, conv, B, cudaMemcpyDeviceToHost, st), "D2H");
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(iters_host, iters, B, cudaMemcpyDeviceToHost, st), "D2H");
+        if (rc) return rc;
+        return cuda_check(cudaStreamSynchronize(st), "stream sync");
+    }
+    HostPipe *hp = nullptr;
+    rc = host_pipe(t->device, &hp);
+    if (rc) return rc;
+    cudaEvent_t ev[2 * kMaxChunks + 1];
+    int made = 0;
+    for (; made < 2 * chunks + 1 && !rc; ++made)
+        rc = cuda_check(cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming), "event");
+    if (!rc) {
+        // the copies start after whatever the caller queued on its stream
+        rc = cuda_check(cudaEventRecord(ev[2 * chunks], st), "event");
+        if (!rc) rc = cuda_check(cudaStreamWaitEvent(hp->h2d, ev[2 * chunks], 0), "wait");
+        if (!rc)
+            rc = cuda_check(cudaMemcpyAsync(prior, prior_host, sizeof(float) * 3 * t->N, cudaMemcpyHostToDevice,
+                                            hp->h2d), "H2D");
+    }
+    for (int c = 0; c < chunks && !rc; ++c) {
+        const int b0 = (int)((long)B * c / chunks), nb = (int)((long)B * (c + 1) / chunks) - b0;
+        rc = cuda_check(cudaMemcpyAsync(syn + W * b0, syn_host + W * b0, sizeof(uint32_t) * W * nb,
+                                        cudaMemcpyHostToDevice, hp->h2d), "H2D");
+        if (!rc) rc = cuda_check(cudaEventRecord(ev[2 * c], hp->h2d), "event");
+        if (!rc) rc = cuda_check(cudaStreamWaitEvent(st, ev[2 * c], 0), "wait");
+        if (!rc)
+            rc = bpq_decode(t, syn + W * b0, prior, variant, params, max_iter, nb, est + N * b0, conv + b0,
+                            iters + b0, work, stream);
+        if (!rc) rc = cuda_check(cudaEventRecord(ev[2 * c + 1], st), "event");
+        if (!rc) rc = cuda_check(cudaStreamWaitEvent(hp->d2h, ev[2 * c + 1], 0), "wait");
+        if (!rc)
+            rc = cuda_check(cudaMemcpyAsync(est_host + N * b0, est + N * b0, N * nb, cudaMemcpyDeviceToHost, hp->d2h),
+                            "D2H");
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(conv_host + b0, conv + b0, nb, cudaMemcpyDeviceToHost, hp->d2h), "D2H");
+        if (!rc)
+            rc = cuda_check(cudaMemcpyAsync(iters_host + b0, iters + b0, nb, cudaMemcpyDeviceToHost, hp->d2h), "D2H");
+    }
+    // drain everything that was queued, also after an error
+    const int rc_d2h = cuda_check(cudaStreamSynchronize(hp->d2h), "stream sync");
+    const int rc_h2d = cuda_check(cudaStreamSynchronize(hp->h2d), "stream sync");
+    const int rc_st = cuda_check(cudaStreamSynchronize(st), "stream sync");
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    return rc ? rc : rc_d2h ? rc_d2h : rc_h2d ? rc_h2d : rc_st;
+}
+
 }  // namespace bpq
 
 extern "C" {
@@ -398,41 +505,8 @@ size_t bpq_decode_host_bytes(const bpq_tanner *t, int B) {
 int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
                     const bpq_params *params, int max_iter, int B, uint8_t *est_host, uint8_t *conv_host,
                     uint8_t *iters_host, void *dev_buf, size_t dev_buf_bytes, void *stream) {
-    int rc = bpq::need_uploaded(t);
-    if (rc) return rc;
-    if (B < 0) return fail(BPQ_EINVAL, "B < 0");
-    if (B == 0) return BPQ_OK;
-    if (!syn_host || !prior_host || !est_host || !conv_host || !iters_host || !dev_buf)
-        return fail(BPQ_EINVAL, "NULL argument");
-    if (dev_buf_bytes < bpq_decode_host_bytes(t, B)) return fail(BPQ_EINVAL, "device buffer too small");
-    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t W = (t->M + 31) / 32;
-    uint8_t *p = static_cast<uint8_t *>(dev_buf);
-    void *work = p;
-    p += al(bpq::kWorkspaceBytes);
-    uint32_t *syn = reinterpret_cast<uint32_t *>(p);
-    p += al(sizeof(uint32_t) * W * B);
-    float *prior = reinterpret_cast<float *>(p);
-    p += al(sizeof(float) * 3 * t->N);
-    uint8_t *est = p;
-    p += al((size_t)B * t->N);
-    uint8_t *conv = p;
-    p += al(B);
-    uint8_t *iters = p;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    rc = bpq::cuda_check(cudaMemcpyAsync(syn, syn_host, sizeof(uint32_t) * W * B, cudaMemcpyHostToDevice, st), "H2D");
-    if (rc) return rc;
-    rc = bpq::cuda_check(cudaMemcpyAsync(prior, prior_host, sizeof(float) * 3 * t->N, cudaMemcpyHostToDevice, st), "H2D");
-    if (rc) return rc;
-    rc = bpq_decode(t, syn, prior, variant, params, max_iter, B, est, conv, iters, work, stream);
-    if (rc) return rc;
-    rc = bpq::cuda_check(cudaMemcpyAsync(est_host, est, (size_t)B * t->N, cudaMemcpyDeviceToHost, st), "D2H");
-    if (rc) return rc;
-    rc = bpq::cuda_check(cudaMemcpyAsync(conv_host, conv, B, cudaMemcpyDeviceToHost, st), "D2H");
-    if (rc) return rc;
-    rc = bpq::cuda_check(cudaMemcpyAsync(iters_host, iters, B, cudaMemcpyDeviceToHost, st), "D2H");
-    if (rc) return rc;
-    return bpq::cuda_check(cudaStreamSynchronize(st), "stream sync");
+    return bpq::decode_host_impl(t, syn_host, prior_host, variant, params, max_iter, B, est_host, conv_host,
+                                 iters_host, dev_buf, dev_buf_bytes, stream, true);
 }
 
 int bpq_decode_host_noalloc(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
@@ -448,8 +522,8 @@ int bpq_decode_host_noalloc(const bpq_tanner *t, const uint32_t *syn_host, const
     void *scratch = nullptr;
     rc = bpq::noalloc_scratch(t->device, &scratch);
     if (rc) return rc;
-    return bpq_decode_host(t, syn_host, prior_host, variant, params, max_iter, B, est_host, conv_host, iters_host,
-                           scratch, bpq::kNoAllocBytes, stream);
+    return bpq::decode_host_impl(t, syn_host, prior_host, variant, params, max_iter, B, est_host, conv_host,
+                                 iters_host, scratch, bpq::kNoAllocBytes, stream, false);
 }
 
 int bpq_decode_host_noalloc_max_shots(const bpq_tanner *t) {

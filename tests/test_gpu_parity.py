@@ -308,6 +308,20 @@ def test_decode_host_matches_device(bpq):
         assert torch.equal(a.cpu(), b)
 
 
+def test_decode_host_pipelined_matches_device(bpq):
+    """A batch large enough for bpq_decode_host's chunked, overlapped copies
+    (with an uneven chunk split) gives the device decode's results."""
+    t = bpq.Tanner("planar", 5)
+    ch = oracle.depolarizing(0.06)
+    B = 5 * 65536 + 123
+    _, syn = bpq.sample(t, *ch, seed=77, shot0=0, B=B)
+    prior = bpq.prior_tensor(t, *ch)
+    dev = bpq.decode(t, syn, prior, "ewainit", max_iter=50)
+    host = bpq.decode_host(t, syn.cpu().pin_memory(), prior.cpu().pin_memory(), "ewainit", max_iter=50)
+    for a, b in zip(dev, host):
+        assert torch.equal(a.cpu(), b)
+
+
 @pytest.mark.parametrize("p,min_stable", [(0.08, 0.75), (0.14, 0.15)])
 def test_full_size_toric_d15_bench_configuration(bpq, p, min_stable):
     """The bench configuration: toric d = 15, 10^6 shots at one p, EWAInit-BP,
