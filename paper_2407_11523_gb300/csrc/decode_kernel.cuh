@@ -245,6 +245,31 @@ __device__ __forceinline__ uint32_t anti_bytes_split(uint32_t d) {
     return (d >= 2u ? 0x00000101u : 0u) | (d - 1u < 2u ? 0x01010000u : 0u);
 }
 
+// The scalars the iteration loop reads, copied once per shot into locals.
+// The one-code kernel reads its DecodeArgs from the constant bank; the
+// batched kernel keeps the descriptor in shared memory, where every slot
+// store could alias it and force a reload on each use.
+struct ShotParams {
+    int N, M, Np, max_iter, ada_from1;
+    float clip2, vclip, alpha, gamma, eps;  // vclip: delta_clip, or phi_clip in the phi form
+};
+
+template <bool PHI>
+__device__ __forceinline__ ShotParams shot_params(const DecodeArgs &a, float alpha) {
+    ShotParams p;
+    p.N = a.N;
+    p.M = a.M;
+    p.Np = a.n_pad;
+    p.max_iter = a.max_iter;
+    p.ada_from1 = a.ada_from1;
+    p.clip2 = a.clip2;
+    p.vclip = PHI ? a.phi_clip : a.delta_clip;
+    p.alpha = alpha;
+    p.gamma = a.gamma;
+    p.eps = a.eps;
+    return p;
+}
+
 // Variable-to-check messages of one qubit (position n of the layout), from
 // its posterior Q and the incoming check-to-variable messages win: stored
 // as sign * delta(|lambda|) (sign * phi(|lambda|) with PHI), the least
@@ -254,8 +279,9 @@ __device__ __forceinline__ uint32_t anti_bytes_split(uint32_t d) {
 // Split layout: slots n * n_pad + j; unused positions are written (as 0)
 // only at t = 0, when ALL is set.
 template <bool TRACE, bool SPLIT, bool PHI, bool ALL>
-__device__ __forceinline__ void emit_v2c(const DecodeArgs &a, float *slots, int j, int t, int shot, uint32_t vp,
-                                         float QX, float QY, float QZ, const float (&win)[4], uint32_t ab) {
+__device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &sp, float *slots, int j, int t,
+                                         int shot, uint32_t vp, float QX, float QY, float QZ, const float (&win)[4],
+                                         uint32_t ab) {
     const float c0 = fminf(0.f, fminf(QX, fminf(QY, QZ)));
     const float e0 = ex2(c0);
     const float eX = ex2(c0 - QX), eY = ex2(c0 - QY), eZ = ex2(c0 - QZ);
@@ -281,22 +307,22 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, float *slots, int 
         float dl;
         if (PHI) {
             const float mx = fmaxf(C, A), mn = fminf(C, A);
-            dl = fmaxf(log1p_rel(2.0f * mn * rcp(mx - mn)), a.phi_clip);
+            dl = fmaxf(log1p_rel(2.0f * mn * rcp(mx - mn)), sp.vclip);
         } else {
-            dl = fmaxf(2.0f * fminf(C, A) * rcp(C + A), a.delta_clip);
+            dl = fmaxf(2.0f * fminf(C, A) * rcp(C + A), sp.vclip);
         }
         const uint32_t bits = (__float_as_uint(dl) & ~1u) | ((ab >> (8 * n)) & 1u) | (A > C ? 0x80000000u : 0u);
         out[n] = p ? __uint_as_float(bits) : 0.f;
         if (TRACE && a.tr_v2c && p) {
             const float lam = fminf(fmaxf(kLn2 * (lg2(C) - lg2(A)), -a.clip), a.clip);
-            const int s = SPLIT ? n * a.n_pad + j : 4 * j + n;
-            a.tr_v2c[((size_t)shot * (a.max_iter + 1) + t) * a.E + a.var_canon[s]] = lam;
+            const int s = SPLIT ? n * sp.Np + j : 4 * j + n;
+            a.tr_v2c[((size_t)shot * (sp.max_iter + 1) + t) * a.E + a.var_canon[s]] = lam;
         }
     }
     if (SPLIT) {
 #pragma unroll
         for (int n = 0; n < 4; ++n)
-            if (ALL || ((vp >> (2 * n)) & 3u)) slots[n * a.n_pad + j] = out[n];
+            if (ALL || ((vp >> (2 * n)) & 3u)) slots[n * sp.Np + j] = out[n];
     } else {
         *reinterpret_cast<float4 *>(slots + 4 * j) = make_float4(out[0], out[1], out[2], out[3]);
     }
@@ -371,7 +397,8 @@ __device__ __forceinline__ GroupMem group_mem(const DecodeArgs &a, uint8_t *base
 template <int VARIANT, int NPT, bool TRACE, bool SPLIT>
 __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<NPT> &adj, const GroupMem &m,
                                            int npt, int T, int tg, int G, int bar_id, int shot, float alpha) {
-    const int N = a.N, M = a.M, Np = a.n_pad;
+    const ShotParams sp = shot_params<PhiForm<VARIANT>::value>(a, alpha);
+    const int N = sp.N, M = sp.M, Np = sp.Np;
     const uint32_t kZero = 4u * (uint32_t)Np, kTrash = kZero + 1u;
     float *slots = m.slots, *state = m.state;
     const float *PiS = m.PiS;
@@ -407,7 +434,7 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                 state[5 * Np + j] = 0.f;
             }
             const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-            emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, true>(a, slots, j, 0, shot, adj.info[k] >> 8, PX, PY,
+            emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, true>(a, sp, slots, j, 0, shot, adj.info[k] >> 8, PX, PY,
                                                                   PZ, z4, 0u);
         }
     }
@@ -415,8 +442,8 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
 
     int conv = 0, iters = 0;
     for (int t = 1;; ++t) {
-        const bool do_check = t > 1 && (!TRACE || t > a.max_iter);
-        const bool do_msgs = t <= a.max_iter;
+        const bool do_check = t > 1 && (!TRACE || t > sp.max_iter);
+        const bool do_msgs = t <= sp.max_iter;
         uint32_t mismatch = 0;
 
         // ---- check pass: syndrome test of the previous decision, then eq. (h_update) ----
@@ -459,11 +486,11 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
                         const float wv = fminf(PhiForm<VARIANT>::value ? phi_check(ext[n]) : c2v_magnitude(ext[n]),
-                                               a.clip2);
+                                               sp.clip2);
                         const float mm = __uint_as_float(__float_as_uint(wv) ^ ((sgn ^ u[n]) & 0x80000000u));
                         slots[sl[n] == kZero ? kTrash : sl[n]] = mm;
                         if (TRACE && a.tr_c2v && sl[n] != kZero)
-                            a.tr_c2v[((size_t)shot * a.max_iter + (t - 1)) * a.E + a.chk_ptr[i] + n] = kLn2 * mm;
+                            a.tr_c2v[((size_t)shot * sp.max_iter + (t - 1)) * a.E + a.chk_ptr[i] + n] = kLn2 * mm;
                     }
                 }
             }
@@ -476,7 +503,7 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
         }
         if (!do_msgs) {
             conv = 0;
-            iters = a.max_iter;
+            iters = sp.max_iter;
             break;
         }
 
@@ -519,8 +546,8 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                         // eqs. (mombp1), (mombp2) with the gradient of (mombp3)
                         const float qp = state[w * Np + j];
                         const float grad = qp - Pi[w] - S[w];
-                        const float g = a.gamma * state[(3 + w) * Np + j] + (1.f - a.gamma) * grad;
-                        Q[w] = qp - a.alpha * g;
+                        const float g = sp.gamma * state[(3 + w) * Np + j] + (1.f - sp.gamma) * grad;
+                        Q[w] = qp - sp.alpha * g;
                         state[w * Np + j] = Q[w];
                         state[(3 + w) * Np + j] = g;
                     } else {
@@ -528,8 +555,8 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                         const float qp = state[w * Np + j];
                         const float gp = qp - Pi[w] - S[w];
                         float Gs = state[(3 + w) * Np + j];
-                        if (t >= 2 || a.ada_from1) Gs += gp * gp;
-                        Q[w] = t == 1 ? Pi[w] + S[w] : qp - a.alpha * gp * rcp(sqrt_approx(Gs) + a.eps);
+                        if (t >= 2 || sp.ada_from1) Gs += gp * gp;
+                        Q[w] = t == 1 ? Pi[w] + S[w] : qp - sp.alpha * gp * rcp(sqrt_approx(Gs) + sp.eps);
                         state[w * Np + j] = Q[w];
                         state[(3 + w) * Np + j] = Gs;
                     }
@@ -549,7 +576,7 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                 // messages' least significant bits)
                 const uint32_t ab = SPLIT ? anti_bytes_split(d) : anti_bytes(d, adj.pp[k]);
                 if (TRACE) {
-                    const size_t o = (size_t)shot * a.max_iter + (t - 1);
+                    const size_t o = (size_t)shot * sp.max_iter + (t - 1);
                     if (a.tr_Q) {
                         a.tr_Q[(o * N + j) * 3 + 0] = kLn2 * Q[0];
                         a.tr_Q[(o * N + j) * 3 + 1] = kLn2 * Q[1];
@@ -557,7 +584,7 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                     }
                     if (a.tr_dec) a.tr_dec[o * N + j] = (uint8_t)d;
                 }
-                emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, false>(a, slots, j, t, shot, vp, Q[0], Q[1], Q[2],
+                emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, false>(a, sp, slots, j, t, shot, vp, Q[0], Q[1], Q[2],
                                                                        win, ab);
             }
         }
