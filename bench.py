@@ -350,6 +350,10 @@ def run_ours(args, rank, world):
     except (OSError, IndexError, ValueError):
         traffic = None
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        hbm_peak = None
     sfu_peak = float("nan") if args.no_probe else bpq.probe_peak("sfu", blocks=sms * 8, threads=256, iters=4096)
     fma_peak = float("nan") if args.no_probe else bpq.probe_peak("fma", blocks=sms * 8, threads=256, iters=4096)
     # EWAInit-BP, delta form, degree-4 qubits: check side rcp + lg2, variable
@@ -364,7 +368,10 @@ def run_ours(args, rank, world):
                 "peak_source": "measured on this GPU by the MUFU.EX2 probe kernel (bpq_probe_peak)",
                 "fma_peak_tinst_per_s": fma_peak / 1e12, "sms": sms,
                 "hbm": {"algorithmic_bytes_per_shot": t.W * 4 + t.N + 2,
-                        "achieved_gbs": (t.W * 4 + t.N + 2) * args.shots_per_p / kernel_sec / 1e9}}
+                        "achieved_gbs": (t.W * 4 + t.N + 2) * args.shots_per_p / kernel_sec / 1e9,
+                        "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                        "frac": ((t.W * 4 + t.N + 2) * args.shots_per_p / kernel_sec / 1e9 / hbm_peak
+                                 if hbm_peak else None)}}
 
     # end to end through bpq_decode_host with pinned host buffers
     e2e = None
