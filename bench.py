@@ -306,12 +306,15 @@ def run_ours(args, rank, world):
                 launch_ms.append(evs[s][k][0].elapsed_time(evs[s][k][1]))
         iters_total = sum(int(o[2].sum(dtype=torch.int64).item()) for o in outs)
         conv = sum(int(o[1].sum(dtype=torch.int64).item()) for o in outs)
+        # iteration histogram over the last step's shots, in bins 1-5, 6-10, ..., 96-100
+        hist = sum(torch.bincount((o[2].long() - 1).clamp(min=0) // 5, minlength=MAX_ITER // 5) for o in outs)
         sec = reduce_max(ms / 1e3, world)
         shots = reduce_sum(float(B * len(P_SWEEP) * args.steps), world)
         eu = reduce_sum(float(iters_total) * t.E * args.steps, world)
         results[v] = {"shots_per_s": shots / sec, "edge_updates_per_s": eu / sec, "ms_per_step": sec * 1e3 / args.steps,
                       "avg_iterations": iters_total / (B * len(P_SWEEP)), "converged_frac": conv / (B * len(P_SWEEP)),
                       "launch_ms_mean": float(np.mean(launch_ms)), "launches": len(launch_ms),
+                      "iteration_histogram_5": [int(x) for x in hist.tolist()],
                       "edge_updates_per_step": iters_total * t.E}
     head = results.get("ewainit") or next(iter(results.values()))
 
