@@ -340,7 +340,7 @@ def run_ours(args, rank, world):
     # roofline of the decode kernel: SFU-bound in-SM arithmetic.  DRAM traffic
     # per shot comes from the committed ncu summary, used only while the
     # kernel source still matches the profiled one.
-    traffic = None
+    traffic = issue_pct = None
     try:
         import hashlib
         prof = open(os.path.join(ROOT, "profiles", "decode_kernel_toric15_ewainit.md")).read()
@@ -350,8 +350,10 @@ def run_ours(args, rank, world):
                          .split("traffic_bytes_per_shot:")[1].split()[0])
         if hashlib.sha256(src).hexdigest()[:16] == want:
             traffic = per_shot * args.shots_per_p
+            issue_pct = float([ln for ln in prof.splitlines() if "issue_active_pct:" in ln][0]
+                              .split("issue_active_pct:")[1].split()[0])
     except (OSError, IndexError, ValueError):
-        traffic = None
+        traffic = issue_pct = None
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     try:
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -368,6 +370,9 @@ def run_ours(args, rank, world):
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": sfu_peak / 1e12, "unit": "TSFUop/s",
                 "frac": achieved / sfu_peak, "traffic": traffic,
                 "kernel": "decode_kernel<EWAINIT>", "per_unit": f"{sfu_per_edge_update} SFU ops per edge-update",
+                "ncu_issue_active_pct": issue_pct,
+                "note": "issue-bound: the SFU is not the binding unit; ncu_issue_active_pct is the share of "
+                        "issue slots used (profiles/decode_kernel_toric15_ewainit.md)",
                 "peak_source": "measured on this GPU by the MUFU.EX2 probe kernel (bpq_probe_peak)",
                 "fma_peak_tinst_per_s": fma_peak / 1e12, "sms": sms,
                 "hbm": {"algorithmic_bytes_per_shot": t.W * 4 + t.N + 2,
