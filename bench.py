@@ -255,12 +255,12 @@ def run_ours(args, rank, world):
     t = bpq.Tanner(CODE, DIST).upload()
     B = args.shots_per_p
     shot0 = shot_offset(rank, B)
-    syns, priors = [], []
+    syns, errs, priors = [], [], []
     for k, p in enumerate(P_SWEEP):
-        _, syn = bpq.sample(t, *[p / 3] * 3, seed=SEED + k, shot0=shot0, B=B)
+        err, syn = bpq.sample(t, *[p / 3] * 3, seed=SEED + k, shot0=shot0, B=B)
         syns.append(syn)
+        errs.append(err)  # kept for the logical error rates, computed after timing
         priors.append(bpq.prior_tensor(t, p / 3, p / 3, p / 3))
-    del _
     outs = [(torch.empty((B, t.N), dtype=torch.uint8, device=dev), torch.empty(B, dtype=torch.uint8, device=dev),
              torch.empty(B, dtype=torch.uint8, device=dev)) for _ in P_SWEEP]
     work = bpq.workspace(dev)
@@ -308,13 +308,24 @@ def run_ours(args, rank, world):
         conv = sum(int(o[1].sum(dtype=torch.int64).item()) for o in outs)
         # iteration histogram over the last step's shots, in bins 1-5, 6-10, ..., 96-100
         hist = sum(torch.bincount((o[2].long() - 1).clamp(min=0) // 5, minlength=MAX_ITER // 5) for o in outs)
+        # logical error rate per p (Sec. IV: failure = not converged, or a logical error), with the
+        # detected / undetected split and a 2-sigma binomial half-width; not timed
+        ler = []
+        for k, p in enumerate(P_SWEEP):
+            f = bpq.check_logical(t, errs[k], outs[k][0])
+            det = reduce_sum(float((f == 1).sum().item()), world)
+            und = reduce_sum(float((f == 2).sum().item()), world)
+            n = float(B * world)
+            r = (det + und) / n
+            ler.append({"p": p, "ler": r, "two_sigma": 2.0 * float(np.sqrt(max(r * (1 - r), 1.0 / n) / n)),
+                        "detected": det / n, "undetected": und / n})
         sec = reduce_max(ms / 1e3, world)
         shots = reduce_sum(float(B * len(P_SWEEP) * args.steps), world)
         eu = reduce_sum(float(iters_total) * t.E * args.steps, world)
         results[v] = {"shots_per_s": shots / sec, "edge_updates_per_s": eu / sec, "ms_per_step": sec * 1e3 / args.steps,
                       "avg_iterations": iters_total / (B * len(P_SWEEP)), "converged_frac": conv / (B * len(P_SWEEP)),
                       "launch_ms_mean": float(np.mean(launch_ms)), "launches": len(launch_ms),
-                      "iteration_histogram_5": [int(x) for x in hist.tolist()],
+                      "iteration_histogram_5": [int(x) for x in hist.tolist()], "ler": ler,
                       "edge_updates_per_step": iters_total * t.E}
     head = results.get("ewainit") or next(iter(results.values()))
 
