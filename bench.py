@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--no-jitter-ler", action="store_true")
     ap.add_argument("--workload", default="toric15", choices=["toric15", "mixed", "serve", "train", "aewa", "serial"],
                     help="toric15: the headline sweep; mixed: many codes in one batched launch; "
                          "serve: continuous-batching server on a Poisson request stream; "
@@ -62,6 +63,9 @@ def parse():
     ap.add_argument("--loads", default="1e4,1e5,1e6,1e7", help="offered loads (requests/s) for --workload serve")
     ap.add_argument("--train-model", default="ewainit", choices=["ewainit", "momentum"],
                     help="unrolled model for --workload train")
+    ap.add_argument("--prior-jitter", type=float, default=0.0,
+                    help="relative per-qubit prior perturbation of the timed toric15 sweep (0: the uniform "
+                         "channel); an untimed EWAInit-BP pass on 2^-16-jittered priors is always reported")
     return ap.parse_args()
 
 
@@ -73,7 +77,8 @@ def workload_config(args):
         "max_iter": MAX_ITER, "headline_variant": "ewainit alpha=0.5",
         "l2": "inputs larger than L2 (syndromes 60 B/shot x 8e6 shots = 480 MB per rank); no flush",
         "parallelism": f"replicas x{args.gpus}: disjoint Philox shot ranges, no data-path collective",
-        "seed": SEED,
+        "seed": SEED, "prior": ("uniform depolarising channel" if not args.prior_jitter else
+                                f"depolarising channel, per-qubit relative jitter {args.prior_jitter}"),
     }
 
 
@@ -260,7 +265,7 @@ def run_ours(args, rank, world):
         err, syn = bpq.sample(t, *[p / 3] * 3, seed=SEED + k, shot0=shot0, B=B)
         syns.append(syn)
         errs.append(err)  # kept for the logical error rates, computed after timing
-        priors.append(bpq.prior_tensor(t, p / 3, p / 3, p / 3))
+        priors.append(bpq.prior_tensor(t, p / 3, p / 3, p / 3, jitter=args.prior_jitter))
     outs = [(torch.empty((B, t.N), dtype=torch.uint8, device=dev), torch.empty(B, dtype=torch.uint8, device=dev),
              torch.empty(B, dtype=torch.uint8, device=dev)) for _ in P_SWEEP]
     work = bpq.workspace(dev)
@@ -328,6 +333,26 @@ def run_ours(args, rank, world):
                       "iteration_histogram_5": [int(x) for x in hist.tolist()], "ler": ler,
                       "edge_updates_per_step": iters_total * t.E}
     head = results.get("ewainit") or next(iter(results.values()))
+
+    # untimed EWAInit-BP pass on priors jittered by 2^-16 per qubit: uniform
+    # priors leave exactly symmetric states that the parallel schedule cannot
+    # break (Sec. V-A), so part of the uniform-prior failures at low p are
+    # rounding-decided ties; the jitter breaks them in the input
+    if "ewainit" in results and not args.no_jitter_ler:
+        rel = 2.0 ** -16
+        params = bpq.make_params("ewainit", **VARIANT_PARAMS["ewainit"])
+        jl, jit_iters = [], 0
+        for k, p in enumerate(P_SWEEP):
+            pj = bpq.prior_tensor(t, p / 3, p / 3, p / 3, jitter=rel)
+            bpq.decode(t, syns[k], pj, "ewainit", params=params, max_iter=MAX_ITER, out=outs[k], work=work)
+            f = bpq.check_logical(t, errs[k], outs[k][0])
+            n = float(B * world)
+            r = reduce_sum(float((f > 0).sum().item()), world) / n
+            jit_iters += int(outs[k][2].sum(dtype=torch.int64).item())
+            jl.append({"p": p, "ler": r, "two_sigma": 2.0 * float(np.sqrt(max(r * (1 - r), 1.0 / n) / n)),
+                       "unconverged": reduce_sum(float((outs[k][1] == 0).sum().item()), world) / n})
+        results["ewainit"]["prior_jitter_2^-16"] = {"ler": jl, "avg_iterations": jit_iters / (B * len(P_SWEEP)),
+                                                    "timed": False}
 
     # p50/p99 launch latency at p = 0.08, EWAInit-BP, batches of 1 and 1024 shots
     lat = {}

@@ -9,6 +9,6 @@ this package is its thin Python binding.
 from ._binding import (  # noqa: F401
     ADAGRAD, AEWA, CODES, EWAINIT, MOMENTUM, PLAIN, PLANAR, TORIC, VARIANTS, XZZX,
     BPQError, BatchPlan, Params, Server, Tanner, autotune, check_logical, decode, decode_host, decode_host_bytes, decode_status,
-    decode_trace, default_params, lib, make_params, prior_tensor, probe_peak, sample, unrolled_loss,
+    decode_trace, default_params, lib, make_params, prior_rows, prior_tensor, probe_peak, sample, unrolled_loss,
     unrolled_posterior, workspace,
 )

@@ -243,10 +243,29 @@ def sample(tanner: Tanner, px, py, pz, seed, shot0, B, err=None, syn=None, strea
     return err, syn
 
 
-def prior_tensor(tanner: Tanner, px, py, pz, device=None) -> torch.Tensor:
-    """(N, 3) float32 probabilities of an i.i.d. channel, on the device."""
+def prior_rows(n_qubits: int, px, py, pz, jitter: float = 0.0) -> np.ndarray:
+    """(N, 3) float32 rows (p^X, p^Y, p^Z) of an i.i.d. channel.  With
+    jitter > 0, row j is scaled by 1 + jitter * u_j, where
+    u_j = 2 * ((j * 2654435761) mod 2^32) / 2^32 - 1 lies in [-1, 1).  The
+    result is computed in float64 and rounded once to float32.
+
+    Uniform priors on the toric and planar codes leave syndromes whose BP
+    state is exactly symmetric (the trapping sets of Sec. II-B2).  Under the
+    parallel schedule EWAInit-BP cannot break such a symmetry by itself
+    (Sec. V-A), so whether a run escapes depends only on the rounding
+    asymmetries of the arithmetic.  A jitter of 2^-16 makes the escape
+    deterministic, and it is far below any channel-estimation precision."""
+    j = np.arange(n_qubits, dtype=np.uint64)
+    u = ((j * np.uint64(2654435761)) % np.uint64(1 << 32)).astype(np.float64) / 2.0 ** 32 * 2.0 - 1.0
+    ch = np.array([px, py, pz], dtype=np.float64)
+    return (ch[None, :] * (1.0 + float(jitter) * u)[:, None]).astype(np.float32)
+
+
+def prior_tensor(tanner: Tanner, px, py, pz, device=None, jitter: float = 0.0) -> torch.Tensor:
+    """(N, 3) float32 probabilities of an i.i.d. channel, on the device;
+    jitter is the relative per-qubit perturbation of prior_rows."""
     tanner.upload()
-    p = torch.tensor([px, py, pz], dtype=torch.float32).repeat(tanner.N, 1)
+    p = torch.from_numpy(prior_rows(tanner.N, px, py, pz, jitter))
     return p.to(device or f"cuda:{tanner.device}")
 
 

@@ -43,6 +43,20 @@ def random_priors(n_qubits: int, seed: int, lo: float = 0.02, hi: float = 0.2):
     return rng.uniform(lo, hi, size=(n_qubits, 3))
 
 
+def jittered_priors(n_qubits: int, px: float, py: float, pz: float, rel: float):
+    """(N, 3) float32 rows (p^X, p^Y, p^Z) of an i.i.d. channel, row j scaled
+    by 1 + rel * u_j with u_j = 2 * ((j * 2654435761) mod 2^32) / 2^32 - 1 in
+    [-1, 1) (Knuth's multiplicative hash of the qubit index).  The arithmetic
+    is done in float64 and rounded once to float32, so the rows are exact
+    and identical wherever they are built.  rel = 0 gives the uniform rows.
+    A tiny rel breaks the exact symmetric ties that uniform priors leave on
+    the toric and planar codes (Sec. II-B2, Sec. V-A)."""
+    j = np.arange(n_qubits, dtype=np.uint64)
+    u = ((j * np.uint64(2654435761)) % np.uint64(1 << 32)).astype(np.float64) / 2.0 ** 32 * 2.0 - 1.0
+    ch = np.array([px, py, pz], dtype=np.float64)
+    return (ch[None, :] * (1.0 + rel * u)[:, None]).astype(np.float32)
+
+
 def random_syndromes(m_checks: int, count: int, seed: int):
     rng = np.random.default_rng(seed)
     return rng.integers(0, 2, size=(count, m_checks)).astype(np.uint8)

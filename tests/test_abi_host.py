@@ -118,3 +118,18 @@ def test_workspace_and_host_buffer_sizes(bpq):
     t = bpq.Tanner("toric", 15)
     n = bpq.decode_host_bytes(t, 1000)
     assert n >= 1000 * (t.N + 2) + 1000 * t.W * 4 + 3 * t.N * 4
+
+
+def test_prior_rows_match_the_shared_input_generator(bpq):
+    from inputs import jittered_priors
+    for n, ch, rel in ((450, (0.02 / 3,) * 3, 2.0 ** -16), (313, (0.01, 0.002, 0.05), 2.0 ** -8), (7, (0.1,) * 3, 0.0)):
+        a = bpq.prior_rows(n, *ch, jitter=rel)
+        b = jittered_priors(n, *ch, rel)
+        assert a.dtype == np.float32 and a.shape == (n, 3)
+        assert np.array_equal(a, b)
+    # the perturbation is relative, bounded by rel, and not constant
+    a = bpq.prior_rows(450, 0.01, 0.01, 0.01, jitter=2.0 ** -16).astype(np.float64)
+    r = a / 0.01 - 1.0
+    assert np.abs(r).max() <= 2.0 ** -16 + 2.0 ** -23 and np.unique(a[:, 0]).size > 300  # float32 resolves about 330 levels here
+    assert (a[:, 0] == a[:, 1]).all() and (a[:, 1] == a[:, 2]).all()
+    assert np.array_equal(bpq.prior_rows(9, 0.01, 0.02, 0.03), np.tile(np.float32([0.01, 0.02, 0.03]), (9, 1)))

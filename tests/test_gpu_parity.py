@@ -210,6 +210,47 @@ def test_decode_planar_d5_10k_shots(bpq, variant):
     assert (fail_g[conv == 1] != 1).all() and (fail_g[conv == 0] == 1).all()
 
 
+@pytest.mark.parametrize("kind,d", [("toric", 10), ("toric", 15), ("planar", 15)])
+def test_low_p_ewainit_on_jittered_priors(bpq, kind, d):
+    """EWAInit-BP at depolarising p = 0.02, 4000 shots, at most 100
+    iterations, on priors jittered by 2^-16 per qubit (prior_rows).  With
+    exactly uniform priors some syndromes leave the decoder in an exactly
+    symmetric state that EWAInit-BP cannot break under the parallel schedule
+    (Sec. V-A), and whether a run escapes then depends only on rounding.  The
+    jitter breaks those ties in the input, so both sides must agree on
+    convergence and on the logical outcome.  Converged estimates that differ
+    must be degenerate equivalents; shots that run to max_iter have no
+    unique answer and are only checked for validity."""
+    from inputs import jittered_priors
+    t = bpq.Tanner(kind, d)
+    H = t.dense()
+    ch = oracle.depolarizing(0.02)
+    B, rel = 4000, 2.0 ** -16
+    err_g, syn_g = bpq.sample(t, *ch, seed=0xB9E00001, shot0=0, B=B)
+    prior_g = bpq.prior_tensor(t, *ch, jitter=rel)
+    rows = jittered_priors(t.N, *ch, rel)
+    assert np.array_equal(prior_g.cpu().numpy(), rows)
+    est, conv, iters = bpq.decode(t, syn_g, prior_g, "ewainit", max_iter=100, alpha=0.5)
+    fail_g = bpq.check_logical(t, err_g, est)
+    torch.cuda.synchronize()
+    est, conv, iters, fail_g = (x.cpu().numpy() for x in (est, conv, iters, fail_g))
+
+    e_ref, s_ref = oracle.sample(H, *ch, seed=0xB9E00001, shot0=0, B=B)
+    est_r, conv_r, _ = oracle.decode(H, s_ref, rows.astype(np.float64), "ewainit", max_iter=100, alpha=0.5,
+                                     nthreads=NTHREADS)
+    fail_r, _ = codes.logical_failure(H, e_ref, est_r)
+    conv = conv.astype(bool)
+    assert (conv == conv_r).mean() >= 0.998, (conv == conv_r).mean()
+    assert ((fail_g > 0) == fail_r).mean() >= 0.998
+    both = conv & conv_r
+    assert (est[both] == est_r[both]).all(axis=1).mean() >= 0.998
+    pg, sg = ler_interval(fail_g > 0)
+    pr, sr = ler_interval(fail_r)
+    assert abs(pg - pr) <= max(sg, sr), (pg, pr)
+    # the jitter leaves almost no shot unconverged at this p
+    assert conv.mean() >= 0.99 and conv_r.mean() >= 0.99
+
+
 @pytest.mark.parametrize("variant", ["adagrad"])
 def test_decode_planar_d5_well_conditioned_adagrad(bpq, variant):
     """AdaGrad-BP with eps = 1 (a well-conditioned boosted step) meets the

@@ -115,3 +115,38 @@ def test_trapping_set_parallel_never_converges(per_pauli):
     tr = oracle.trace(H, syn, prior, variant="plain", T=T)
     seen = {tuple(r) for r in tr["dec"]}
     assert (0, 0, 0, 0) in seen and (1, 1, 1, 1) in seen
+
+
+def test_prior_jitter_breaks_the_exact_symmetry():
+    """Under the parallel schedule EWAInit-BP cannot leave the symmetric
+    (4,0) trapping set by itself (Sec. V-A); any asymmetry in the input priors
+    is amplified by the prior re-initialisation of eq. (EWAInit) until the
+    decisions split and satisfy the syndrome.  Plain BP has no such
+    amplification and keeps oscillating."""
+    from inputs import jittered_priors
+    H = trapping_set_code()
+    syn = np.array([[1, 0, 1, 0]], dtype=np.uint8)
+    prior = jittered_priors(4, *oracle.depolarizing(0.01), 2.0 ** -16).astype(np.float64)
+    est, conv, iters = oracle.decode(H, syn, prior, variant="ewainit", max_iter=50)
+    assert conv[0] and iters[0] < 50
+    assert np.array_equal(codes.syndrome(H, est[0]), syn[0])
+    assert len(set(est[0].tolist())) == 2  # the decisions are no longer all equal
+    _, conv, _ = oracle.decode(H, syn, prior, variant="plain", max_iter=50)
+    assert not conv[0]
+
+
+def test_uniform_priors_leave_tie_failures_on_the_toric_code():
+    """Toric d = 6 at p = 0.02: every EWAInit-BP non-convergence with uniform
+    priors is an exact-symmetry tie.  A relative per-qubit jitter of 2^-16
+    converts all of them to converged estimates and loses no shot that
+    converged before."""
+    from inputs import jittered_priors
+    H, _ = codes.build_code("toric", 6)
+    ch = oracle.depolarizing(0.02)
+    _, syn = oracle.sample(H, *ch, seed=0xB9E00001, shot0=0, B=2000)
+    conv = {}
+    for rel in (0.0, 2.0 ** -16):
+        prior = jittered_priors(H.shape[1], *ch, rel).astype(np.float64)
+        _, conv[rel], _ = oracle.decode(H, syn, prior, variant="ewainit", max_iter=100)
+    assert (~conv[0.0]).sum() >= 5
+    assert conv[2.0 ** -16].all()
