@@ -231,7 +231,7 @@ int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prio
     if (max_iter < 1 || max_iter > 255) return fail(BPQ_EINVAL, "max_iter must be in [1, 255]");
     if (B > 0 && (!syn || !prior || !work)) return fail(BPQ_EINVAL, "NULL input or workspace");
     std::memset(&a, 0, sizeof a);
-    a.split = t->split ? 1 : 0;
+    a.split = t->full ? 2 : t->split ? 1 : 0;
     a.table = t->split ? t->d_table_split : t->d_table;
     a.table_bytes = (uint32_t)t->table.size();
     a.off_chk_pauli = t->off_chk_pauli;

@@ -57,6 +57,10 @@ struct bpq_tanner {
     // format, but slot p * n4 + j (n4 = N rounded up to 4) holds qubit j's
     // p-th edge with positions 0, 1 its X edges and 2, 3 its Z edges.
     bool split = false;
+    // Split layout with every slot in use: every check has four edges and
+    // every qubit two X and two Z edges (the toric codes), so the decoder
+    // needs no padding slots.
+    bool full = false;
     std::vector<uint8_t> table_split;
     std::vector<int32_t> var_canon_split;  // 4 n4, indexed by split slot
     // Serial schedule (bpq::build_serial_table): SerialVar[N] in level order |

@@ -9,17 +9,16 @@ namespace bpq {
 
 namespace {
 
-int state_arrays(int variant) {
-    return variant == BPQ_PLAIN ? 0 : (variant == BPQ_EWAINIT || variant == BPQ_AEWA) ? 3 : 6;
-}
+int state_arrays(int variant) { return decode_state_arrays(variant); }
 
-DecodeKernelFn pick(int variant, int npt, bool trace, bool split) {
+DecodeKernelFn pick(int variant, int npt, bool trace, int layout) {
+    const bool split = layout != 0, full = layout == 2 && !trace;
     switch (variant) {
-        case BPQ_PLAIN: return pick_plain(npt, trace, split);
-        case BPQ_MOMENTUM: return pick_momentum(npt, trace, split);
-        case BPQ_ADAGRAD: return pick_adagrad(npt, trace, split);
-        case BPQ_EWAINIT: return pick_ewainit(npt, trace, split);
-        case BPQ_AEWA: return pick_aewa(npt, trace, split);
+        case BPQ_PLAIN: return full ? pick_plain_full(npt) : pick_plain(npt, trace, split);
+        case BPQ_MOMENTUM: return full ? pick_momentum_full(npt) : pick_momentum(npt, trace, split);
+        case BPQ_ADAGRAD: return full ? pick_adagrad_full(npt) : pick_adagrad(npt, trace, split);
+        case BPQ_EWAINIT: return full ? pick_ewainit_full(npt) : pick_ewainit(npt, trace, split);
+        case BPQ_AEWA: return full ? pick_aewa_full(npt) : pick_aewa(npt, trace, split);
     }
     return nullptr;
 }
@@ -86,7 +85,7 @@ int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, c
     LaunchShape s;
     int rc = decode_launch_shape(t, variant, &s);
     if (rc) return rc;
-    DecodeKernelFn fn = pick(variant, s.npt, trace, a.split != 0);
+    DecodeKernelFn fn = pick(variant, s.npt, trace, a.split);
     if (!fn) return fail(BPQ_EINVAL, "no kernel for this variant (AEWA-BP has no trace mode)");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));

@@ -166,10 +166,12 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // |w| = 2 atanh(1 - D) = ln((2 - D) / D).
 __device__ __forceinline__ float oplus(float a, float b) { return fmaf(-a, b, a + b); }
 
-// |m_{c->v}| = log2((2 - D) / D) in bits (see the unit note at the top), D in
-// [0, 1]; D = 0 (only certain incoming messages, e.g. a degree-1 check) gives
-// +inf, clipped by the caller.
-__device__ __forceinline__ float c2v_magnitude(float D) { return lg2((2.0f - D) * rcp(D)); }
+// |m_{c->v}| = log2((2 - D) / D) = log2(2/D - 1) in bits (see the unit note
+// at the top), D in [0, 1]: the rcp error (2^-22 relative) gives an absolute
+// error below 2^-21 in 2/D - 1 near D = 1 and a relative one for small D.
+// D = 0 (only certain incoming messages, e.g. a degree-1 check) gives +inf,
+// clipped by the caller.
+__device__ __forceinline__ float c2v_magnitude(float D) { return lg2(fmaf(2.0f, rcp(D), -1.0f)); }
 
 // AdaGrad-BP keeps Gallager's form instead: v->c messages stored as
 // sign * phi(|m|), phi(x) = -ln tanh(x/2) (its own inverse), summed by the
@@ -208,11 +210,11 @@ __device__ __forceinline__ float log1p_rel(float r) {
     return r < 0.0625f ? poly : big;
 }
 
-// Number of per-qubit state arrays a variant keeps in shared memory:
-// EWAInit Q^(t-1); Momentum Q^(t-1), g; AdaGrad Q^(t-1), G.
+// Number of per-qubit state arrays a variant keeps in shared memory
+// (decode_state_arrays).
 template <int VARIANT>
 struct StateArrays {
-    static constexpr int n = VARIANT == BPQ_PLAIN ? 0 : (VARIANT == BPQ_EWAINIT || VARIANT == BPQ_AEWA) ? 3 : 6;
+    static constexpr int n = decode_state_arrays(VARIANT);
 };
 
 // Sum of the c->v messages from checks that anticommute with X, Y, Z
@@ -241,8 +243,9 @@ __device__ __forceinline__ uint32_t anti_bytes(uint32_t d, uint32_t pp) {
 
 // The same for the split layout, where positions 0, 1 hold X edges and 2, 3
 // Z edges: X anticommutes with Y, Z (d >= 2) and Z with X, Y (d in {1, 2}).
-__device__ __forceinline__ uint32_t anti_bytes_split(uint32_t d) {
-    return (d >= 2u ? 0x00000101u : 0u) | (d - 1u < 2u ? 0x01010000u : 0u);
+// Bit 0: the X positions' bit; bit 1: the Z positions'.
+__device__ __forceinline__ uint32_t anti_bits_split(uint32_t d) {
+    return (d >= 2u ? 1u : 0u) | (d - 1u < 2u ? 2u : 0u);
 }
 
 // The scalars the iteration loop reads, copied once per shot into locals.
@@ -273,12 +276,13 @@ __device__ __forceinline__ ShotParams shot_params(const DecodeArgs &a, float alp
 // Variable-to-check messages of one qubit (position n of the layout), from
 // its posterior Q and the incoming check-to-variable messages win: stored
 // as sign * delta(|lambda|) (sign * phi(|lambda|) with PHI), the least
-// significant bit replaced by byte n of ab (whether this iteration's
-// decision anticommutes with the edge), which the next check pass reads for
-// the syndrome test.  Generic layout: slots 4j .. 4j+3, one float4 store.
+// significant bit replaced by whether this iteration's decision
+// anticommutes with the edge (byte n of ab in the generic layout; bit 0 of
+// ab for positions 0, 1 and bit 1 for positions 2, 3 in the split one),
+// which the next check pass reads for the syndrome test.  Generic layout: slots 4j .. 4j+3, one float4 store.
 // Split layout: slots n * n_pad + j; unused positions are written (as 0)
-// only at t = 0, when ALL is set.
-template <bool TRACE, bool SPLIT, bool PHI, bool ALL>
+// only at t = 0, when ALL is set.  FULL: every position is used.
+template <bool TRACE, bool SPLIT, bool PHI, bool ALL, bool FULL>
 __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &sp, float *slots, int j, int t,
                                          int shot, uint32_t vp, float QX, float QY, float QZ, const float (&win)[4],
                                          uint32_t ab) {
@@ -311,8 +315,9 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &
         } else {
             dl = fmaxf(2.0f * fminf(C, A) * rcp(C + A), sp.vclip);
         }
-        const uint32_t bits = (__float_as_uint(dl) & ~1u) | ((ab >> (8 * n)) & 1u) | (A > C ? 0x80000000u : 0u);
-        out[n] = p ? __uint_as_float(bits) : 0.f;
+        const uint32_t abit = SPLIT ? (n < 2 ? ab & 1u : ab >> 1) : (ab >> (8 * n)) & 1u;
+        const uint32_t bits = (__float_as_uint(dl) & ~1u) | abit | (A > C ? 0x80000000u : 0u);
+        out[n] = (FULL || p) ? __uint_as_float(bits) : 0.f;
         if (TRACE && a.tr_v2c && p) {
             const float lam = fminf(fmaxf(kLn2 * (lg2(C) - lg2(A)), -a.clip), a.clip);
             const int s = SPLIT ? n * sp.Np + j : 4 * j + n;
@@ -322,7 +327,7 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &
     if (SPLIT) {
 #pragma unroll
         for (int n = 0; n < 4; ++n)
-            if (ALL || ((vp >> (2 * n)) & 3u)) slots[n * sp.Np + j] = out[n];
+            if (ALL || FULL || ((vp >> (2 * n)) & 3u)) slots[n * sp.Np + j] = out[n];
     } else {
         *reinterpret_cast<float4 *>(slots + 4 * j) = make_float4(out[0], out[1], out[2], out[3]);
     }
@@ -393,8 +398,10 @@ __device__ __forceinline__ GroupMem group_mem(const DecodeArgs &a, uint8_t *base
 // Decode one shot with a group of G warps (thread tg of 32G): eq. (init),
 // then iterations of the check pass and the variable pass until the hard
 // decision satisfies the syndrome or max_iter is reached; writes the shot's
-// outputs.  npt <= NPT is the number of nodes each thread owns.
-template <int VARIANT, int NPT, bool TRACE, bool SPLIT>
+// outputs.  npt <= NPT is the number of nodes each thread owns.  FULL
+// (split layout only): every check has four edges and every qubit two X and
+// two Z edges, so no edge is padding.
+template <int VARIANT, int NPT, bool TRACE, bool SPLIT, bool FULL>
 __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<NPT> &adj, const GroupMem &m,
                                            int npt, int T, int tg, int G, int bar_id, int shot, float alpha) {
     const ShotParams sp = shot_params<PhiForm<VARIANT>::value>(a, alpha);
@@ -415,7 +422,8 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
     }
 
     // eq. (init): lambda(Pi^(0)), i.e. the variable pass with Q = Pi^(0)
-    // and no incoming messages; Q^(0) = Pi^(0), g^(0) = G^(0) = 0
+    // and no incoming messages; Q^(0) = Pi^(0), g^(0) = G^(0) = 0; EWAInit
+    // starts from Pi^(1) = Pi^(0) and keeps alpha Pi^(0)
     uint32_t dk[NPT];
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
@@ -428,14 +436,18 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                 state[Np + j] = PY;
                 state[2 * Np + j] = PZ;
             }
-            if (StateArrays<VARIANT>::n == 6) {
+            if (VARIANT == BPQ_EWAINIT) {
+                state[3 * Np + j] = alpha * PX;
+                state[4 * Np + j] = alpha * PY;
+                state[5 * Np + j] = alpha * PZ;
+            } else if (StateArrays<VARIANT>::n == 6) {
                 state[3 * Np + j] = 0.f;
                 state[4 * Np + j] = 0.f;
                 state[5 * Np + j] = 0.f;
             }
             const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-            emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, true>(a, sp, slots, j, 0, shot, adj.info[k] >> 8, PX, PY,
-                                                                  PZ, z4, 0u);
+            emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, true, FULL>(a, sp, slots, j, 0, shot, adj.info[k] >> 8,
+                                                                        PX, PY, PZ, z4, 0u);
         }
     }
     group_sync(G, bar_id);
@@ -485,10 +497,14 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                     }
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
-                        const float wv = fminf(PhiForm<VARIANT>::value ? phi_check(ext[n]) : c2v_magnitude(ext[n]),
-                                               sp.clip2);
+                        // every incoming delta is at least delta_clip, so without
+                        // padding (FULL) the delta-form magnitude is at most
+                        // msg_clip already (up to rounding); padded edges read
+                        // delta = 0 and need the clip
+                        const float w0 = PhiForm<VARIANT>::value ? phi_check(ext[n]) : c2v_magnitude(ext[n]);
+                        const float wv = FULL && !PhiForm<VARIANT>::value ? w0 : fminf(w0, sp.clip2);
                         const float mm = __uint_as_float(__float_as_uint(wv) ^ ((sgn ^ u[n]) & 0x80000000u));
-                        slots[sl[n] == kZero ? kTrash : sl[n]] = mm;
+                        slots[FULL ? sl[n] : sl[n] == kZero ? kTrash : sl[n]] = mm;
                         if (TRACE && a.tr_c2v && sl[n] != kZero)
                             a.tr_c2v[((size_t)shot * sp.max_iter + (t - 1)) * a.E + a.chk_ptr[i] + n] = kLn2 * mm;
                     }
@@ -537,11 +553,10 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                     if (VARIANT == BPQ_PLAIN) {
                         Q[w] = Pi[w] + S[w];  // eq. (p_update)
                     } else if (VARIANT == BPQ_EWAINIT) {
-                        // eq. (EWAInit): Pi^(t) = alpha Pi^(0) + (1-alpha) Q^(t-1), t > 1
-                        const float qp = state[w * Np + j];
-                        const float pit = t > 1 ? alpha * Pi[w] + (1.f - alpha) * qp : Pi[w];
-                        Q[w] = pit + S[w];
-                        state[w * Np + j] = Q[w];
+                        // eq. (EWAInit): the state holds Pi^(t) (Pi^(0) at t = 1);
+                        // Pi^(t+1) = alpha Pi^(0) + (1-alpha) Q^(t)
+                        Q[w] = state[w * Np + j] + S[w];
+                        state[w * Np + j] = fmaf(1.f - alpha, Q[w], state[(3 + w) * Np + j]);
                     } else if (VARIANT == BPQ_MOMENTUM) {
                         // eqs. (mombp1), (mombp2) with the gradient of (mombp3)
                         const float qp = state[w * Np + j];
@@ -562,19 +577,13 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                     }
                 }
                 // hard decision: I if all Q_W > 0, else the first minimum of X, Y, Z
-                uint32_t d;
-                if (Q[0] > 0.f && Q[1] > 0.f && Q[2] > 0.f) {
-                    d = 0;
-                } else {
-                    d = 1;
-                    float mq = Q[0];
-                    if (Q[1] < mq) { d = 2; mq = Q[1]; }
-                    if (Q[2] < mq) d = 3;
-                }
+                // (the minimum is shared with emit_v2c's c0)
+                const float mq = fminf(Q[0], fminf(Q[1], Q[2]));
+                const uint32_t d = mq > 0.f ? 0u : Q[0] == mq ? 1u : Q[1] == mq ? 2u : 3u;
                 dk[k] = d;
                 // per-edge <E^_j, H_ij> for the next syndrome test (carried in the
                 // messages' least significant bits)
-                const uint32_t ab = SPLIT ? anti_bytes_split(d) : anti_bytes(d, adj.pp[k]);
+                const uint32_t ab = SPLIT ? anti_bits_split(d) : anti_bytes(d, adj.pp[k]);
                 if (TRACE) {
                     const size_t o = (size_t)shot * sp.max_iter + (t - 1);
                     if (a.tr_Q) {
@@ -584,8 +593,8 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                     }
                     if (a.tr_dec) a.tr_dec[o * N + j] = (uint8_t)d;
                 }
-                emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, false>(a, sp, slots, j, t, shot, vp, Q[0], Q[1], Q[2],
-                                                                       win, ab);
+                emit_v2c<TRACE, SPLIT, PhiForm<VARIANT>::value, false, FULL>(a, sp, slots, j, t, shot, vp, Q[0], Q[1],
+                                                                             Q[2], win, ab);
             }
         }
         group_sync(G, bar_id);
@@ -608,7 +617,7 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
 
 // One code per launch: a persistent grid; every shot group takes shots from
 // the global queue until the batch is exhausted.
-template <int VARIANT, int NPT, bool TRACE, bool SPLIT>
+template <int VARIANT, int NPT, bool TRACE, bool SPLIT, bool FULL = false>
 __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
@@ -654,11 +663,11 @@ __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const 
             // Appendix C: EWAInit-BP with alpha = 1.0, 0.9, ..., 0.0 in turn until
             // a run converges (the outputs are those of the last run)
             for (int k = 0; k <= 10; ++k)
-                if (decode_shot<BPQ_EWAINIT, NPT, TRACE, SPLIT>(a, adj, m, NPT, T, tg, G, bar_id, shot,
-                                                              1.0f - 0.1f * (float)k))
+                if (decode_shot<BPQ_EWAINIT, NPT, TRACE, SPLIT, FULL>(a, adj, m, NPT, T, tg, G, bar_id, shot,
+                                                                    1.0f - 0.1f * (float)k))
                     break;
         } else {
-            decode_shot<VARIANT, NPT, TRACE, SPLIT>(a, adj, m, NPT, T, tg, G, bar_id, shot, a.alpha);
+            decode_shot<VARIANT, NPT, TRACE, SPLIT, FULL>(a, adj, m, NPT, T, tg, G, bar_id, shot, a.alpha);
         }
     }
 }
@@ -743,10 +752,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
                 group_sync(G, bar_id);
                 const int shot = grp_shot[group];
                 if (shot >= a.B) break;
+                // (codes without padding run the padded split-layout code
+                // here, with the same results: a third inlined copy would add
+                // code to a kernel already at its 64-register cap)
                 if (a.split)
-                    decode_shot<VARIANT, NPT, false, true>(a, adj, m, a.npt, T, tg, G, bar_id, shot, a.alpha);
+                    decode_shot<VARIANT, NPT, false, true, false>(a, adj, m, a.npt, T, tg, G, bar_id, shot, a.alpha);
                 else
-                    decode_shot<VARIANT, NPT, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, shot, a.alpha);
+                    decode_shot<VARIANT, NPT, false, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, shot,
+                                                                   a.alpha);
             }
         }
         __syncthreads();
@@ -757,7 +770,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
 
 // AEWA-BP: single-code, non-trace kernels only.
 #define BPQ_DEFINE_PICK_AEWA(NAME)                                                       \
-    DecodeKernelFn NAME(int npt, bool trace, bool split) {                                 \
+    DecodeKernelFn NAME(int npt, bool trace, bool split) {                               \
         if (trace) return nullptr;                                                       \
         switch (npt) {                                                                   \
             case 1: return split ? dk::decode_kernel<BPQ_AEWA, 1, false, true>             \
@@ -777,7 +790,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
 #define BPQ_PICK_NPT(V, NPT, TR)                                                         \
     (split ? dk::decode_kernel<V, NPT, TR, true> : dk::decode_kernel<V, NPT, TR, false>)
 #define BPQ_DEFINE_PICK(NAME, V)                                                         \
-    DecodeKernelFn NAME(int npt, bool trace, bool split) {                                 \
+    DecodeKernelFn NAME(int npt, bool trace, bool split) {                               \
         switch (npt * 2 + (trace ? 1 : 0)) {                                             \
             case 2: return BPQ_PICK_NPT(V, 1, false);                                    \
             case 3: return BPQ_PICK_NPT(V, 1, true);                                     \
@@ -792,6 +805,20 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
     }                                                                                    \
     BatchKernelFn NAME##_batch(int npt) {                                                \
         return npt <= 2 ? dk::decode_batch_kernel<V, 2> : nullptr;                       \
+    }
+
+// The non-trace kernels of one variant for split tables without padding
+// (bpq_tanner::full), instantiated in translation units of their own so
+// that they compile in parallel with the others.
+#define BPQ_DEFINE_PICK_FULL(NAME, V)                                                    \
+    DecodeKernelFn NAME(int npt) {                                                       \
+        switch (npt) {                                                                   \
+            case 1: return dk::decode_kernel<V, 1, false, true, true>;                   \
+            case 2: return dk::decode_kernel<V, 2, false, true, true>;                   \
+            case 3: return dk::decode_kernel<V, 3, false, true, true>;                   \
+            case 4: return dk::decode_kernel<V, 4, false, true, true>;                   \
+        }                                                                                \
+        return nullptr;                                                                  \
     }
 
 }  // namespace bpq

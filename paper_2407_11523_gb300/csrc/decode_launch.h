@@ -10,6 +10,12 @@
 
 namespace bpq {
 
+// Per-qubit state arrays (each n_pad floats) a shot group of the flooding
+// kernels keeps in shared memory: EWAInit the next prior Pi^(t+1) and
+// alpha Pi^(0); Momentum Q^(t-1), g; AdaGrad Q^(t-1), G.  The kernels and the
+// host's shared-memory sizing both read this.
+__host__ __device__ constexpr int decode_state_arrays(int variant) { return variant == BPQ_PLAIN ? 0 : 6; }
+
 constexpr uint32_t kSmemHeader = 256;  // mbarrier, current item, per-group shot indices
 constexpr int kMaxGroupsPerCta = 32;   // named barriers limit multi-warp groups to 15
 
@@ -31,7 +37,8 @@ struct DecodeArgs {
     float alpha, gamma, eps, clip, delta_clip, phi_clip;
     float clip2;               // msg_clip in bits (msg_clip log2 e)
     int ada_from1;
-    int split;                 // table in the split layout (bpq_tanner::split)
+    int split;                 // 0: generic layout; 1: split layout (bpq_tanner::split);
+                               // 2: split layout with every slot used (bpq_tanner::full)
     // used by the batched kernel only
     int npt, groups_per_cta;
 };
@@ -65,15 +72,21 @@ using DecodeKernelFn = void (*)(const DecodeArgs);
 using BatchKernelFn = void (*)(const BatchArgs);
 
 // Kernels of one variant, for nodes per thread npt in [1, 4]; split selects the
-// specialisation for tables in the split layout.
+// specialisation for tables in the split layout, and the _full functions the
+// non-trace kernels for split tables without padding.
 DecodeKernelFn pick_plain(int npt, bool trace, bool split);
+DecodeKernelFn pick_plain_full(int npt);
 BatchKernelFn pick_plain_batch(int npt);
 DecodeKernelFn pick_momentum(int npt, bool trace, bool split);
+DecodeKernelFn pick_momentum_full(int npt);
 BatchKernelFn pick_momentum_batch(int npt);
 DecodeKernelFn pick_adagrad(int npt, bool trace, bool split);
+DecodeKernelFn pick_adagrad_full(int npt);
 BatchKernelFn pick_adagrad_batch(int npt);
 DecodeKernelFn pick_ewainit(int npt, bool trace, bool split);
+DecodeKernelFn pick_ewainit_full(int npt);
 DecodeKernelFn pick_aewa(int npt, bool trace, bool split);
+DecodeKernelFn pick_aewa_full(int npt);
 BatchKernelFn pick_ewainit_batch(int npt);
 
 int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s);

@@ -60,6 +60,13 @@ namespace sk {
 
 using namespace dk;
 
+// Per-qubit state arrays (each n_pad floats) of the serial kernel in a warp's
+// shared memory: EWAInit Q^(t-1); Momentum Q^(t-1), g; AdaGrad Q^(t-1), G.
+// The kernel and serial_launch's sizing both read this.
+__host__ __device__ constexpr int serial_state_arrays(int variant) {
+    return variant == BPQ_PLAIN ? 0 : variant == BPQ_EWAINIT ? 3 : 6;
+}
+
 // Shared memory of one warp: messages | state | syndrome words | decisions.
 struct WarpMem {
     float *msg, *state;
@@ -209,12 +216,12 @@ __device__ __forceinline__ void decode_serial_shot(const SerialArgs &a, const Wa
         const SerialVar sv = vars[v];
         const int j = sv.j;
         const float PX = PiS[j], PY = PiS[Np + j], PZ = PiS[2 * Np + j];
-        if (StateArrays<VARIANT>::n >= 3) {
+        if (serial_state_arrays(VARIANT) >= 3) {
             m.state[j] = PX;
             m.state[Np + j] = PY;
             m.state[2 * Np + j] = PZ;
         }
-        if (StateArrays<VARIANT>::n == 6) {
+        if (serial_state_arrays(VARIANT) == 6) {
             m.state[3 * Np + j] = 0.f;
             m.state[4 * Np + j] = 0.f;
             m.state[5 * Np + j] = 0.f;
@@ -321,8 +328,6 @@ SerialKernelFn pick_serial(int variant, bool trace) {
 
 namespace {
 
-int state_arrays_of(int variant) { return variant == BPQ_PLAIN ? 0 : variant == BPQ_EWAINIT ? 3 : 6; }
-
 // Validate, fill the arguments from the parallel decoder's (parameters in
 // the kernel's units) and launch.
 int serial_launch(const bpq_tanner *t, const uint32_t *syn, const float *prior, int variant, const bpq_params *params,
@@ -362,7 +367,7 @@ int serial_launch(const bpq_tanner *t, const uint32_t *syn, const float *prior, 
     a.max_iter = max_iter;
     a.n_pad = (t->N + 3) & ~3;
     a.msg_floats = (uint32_t)((t->E + 1 + 3) & ~3);
-    const uint32_t state_bytes = 4u * (uint32_t)(state_arrays_of(variant) * a.n_pad);
+    const uint32_t state_bytes = 4u * (uint32_t)(sk::serial_state_arrays(variant) * a.n_pad);
     a.off_syn = 4u * a.msg_floats + state_bytes;
     a.off_est = a.off_syn + 4u * (uint32_t)((a.W + 3) & ~3);
     a.warp_bytes = (a.off_est + (uint32_t)t->N + 15u) & ~15u;

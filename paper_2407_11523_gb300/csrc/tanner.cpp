@@ -113,6 +113,16 @@ int build_tables(bpq_tanner *t) {
         }
         if (nx > 2 || nz > 2) t->split = false;
     }
+    t->full = t->split;
+    for (int i = 0; i < M && t->full; ++i) t->full = t->chk_ptr[i + 1] - t->chk_ptr[i] == 4;
+    for (int j = 0; j < N && t->full; ++j) {
+        int nx = 0, nz = 0;
+        for (int e : var_edges[j]) {
+            nx += t->chk_pauli[e] == 1;
+            nz += t->chk_pauli[e] == 3;
+        }
+        t->full = nx == 2 && nz == 2;
+    }
     t->table_split.clear();
     t->var_canon_split.clear();
     if (t->split) {

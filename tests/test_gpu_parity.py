@@ -283,6 +283,28 @@ def test_launch_shapes_give_identical_results(bpq):
             assert torch.equal(a, b), (s, v)
 
 
+def test_full_layout_kernel_matches_padded_kernel(bpq):
+    """Toric codes (every check of degree 4, every qubit with two X and two Z
+    edges) run the kernel without padding slots.  The same code with one
+    extra isolated qubit runs the padded split-layout kernel; every edge's
+    arithmetic is the same, so the results on the code's own qubits must be
+    bit-identical."""
+    t = bpq.Tanner("toric", 9)
+    H = t.dense()
+    Hx = np.concatenate([H, np.zeros((H.shape[0], 1), dtype=np.uint8)], axis=1)
+    tx = bpq.Tanner(H=Hx)
+    ch = oracle.depolarizing(0.08)
+    _, syn = bpq.sample(t, *ch, seed=3, shot0=0, B=3000)
+    prior = bpq.prior_tensor(t, *ch)
+    prior_x = torch.cat([prior, prior[:1]]).contiguous()
+    for v in VARIANTS:
+        a = bpq.decode(t, syn, prior, variant=v, max_iter=60)
+        b = bpq.decode(tx, syn, prior_x, variant=v, max_iter=60)
+        assert torch.equal(a[0], b[0][:, :t.N]), v
+        assert (b[0][:, t.N] == 0).all()
+        assert torch.equal(a[1], b[1]) and torch.equal(a[2], b[2]), v
+
+
 def test_shot_partition_invariance(bpq):
     t = bpq.Tanner("planar", 9)
     ch = oracle.depolarizing(0.08)
