@@ -165,6 +165,10 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // when every delta is small (confident messages), and
 // |w| = 2 atanh(1 - D) = ln((2 - D) / D).
 __device__ __forceinline__ float oplus(float a, float b) { return fmaf(-a, b, a + b); }
+// Two (+) at once with packed f32x2 instructions, each lane rounded as oplus.
+__device__ __forceinline__ float2 oplus2(float2 a, float2 b) {
+    return __ffma2_rn(make_float2(-a.x, -a.y), b, __fadd2_rn(a, b));
+}
 
 // |m_{c->v}| = log2((2 - D) / D) = log2(2/D - 1) in bits (see the unit note
 // at the top), D in [0, 1]: the rcp error (2^-22 relative) gives an absolute
@@ -292,34 +296,54 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &
     // C = 1 + e^{-Q_H} and the two anticommuting terms, for H = X, Y, Z
     const float CX = e0 + eX, CY = e0 + eY, CZ = e0 + eZ;
     const float AX = eY + eZ, AY = eX + eZ, AZ = eX + eY;
+    float C[4], Ab[4], x[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        const uint32_t p = (vp >> (2 * n)) & 3u;
+        if (SPLIT) {
+            C[n] = n < 2 ? CX : CZ;
+            Ab[n] = n < 2 ? AX : AZ;
+        } else {
+            C[n] = p == 1u ? CX : p == 2u ? CY : CZ;
+            Ab[n] = p == 1u ? AX : p == 2u ? AY : AZ;
+        }
+        x[n] = ex2(win[n]);
+    }
+    // lambda = ln(C / A), A = Ab e^{m_in}; delta = 1 - tanh(|lambda|/2) =
+    // 2 min(C, A) / (C + A), at least delta_clip; or phi(|lambda|) =
+    // log1p(2 min(C, A) / |C - A|), at least phi_clip (|lambda| <= msg_clip).
+    // Edges n, n+1 share packed two-lane fp32 instructions (f32x2): each lane
+    // rounds as the scalar operation would.
+    float A[4], dl[4];
+#pragma unroll
+    for (int n = 0; n < 4; n += 2) {
+        const float2 A2 = __fmul2_rn(make_float2(Ab[n], Ab[n + 1]), make_float2(x[n], x[n + 1]));
+        A[n] = A2.x;
+        A[n + 1] = A2.y;
+        if (PHI) {
+#pragma unroll
+            for (int h = n; h < n + 2; ++h) {
+                const float mx = fmaxf(C[h], A[h]), mn = fminf(C[h], A[h]);
+                dl[h] = fmaxf(log1p_rel(2.0f * mn * rcp(mx - mn)), sp.vclip);
+            }
+        } else {
+            const float2 s2 = __fadd2_rn(make_float2(C[n], C[n + 1]), A2);
+            const float m0 = fminf(C[n], A2.x), m1 = fminf(C[n + 1], A2.y);
+            const float2 d2 = __fmul2_rn(__fadd2_rn(make_float2(m0, m1), make_float2(m0, m1)),
+                                         make_float2(rcp(s2.x), rcp(s2.y)));
+            dl[n] = fmaxf(d2.x, sp.vclip);
+            dl[n + 1] = fmaxf(d2.y, sp.vclip);
+        }
+    }
     float out[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
         const uint32_t p = (vp >> (2 * n)) & 3u;
-        float C, Ab;
-        if (SPLIT) {
-            C = n < 2 ? CX : CZ;
-            Ab = n < 2 ? AX : AZ;
-        } else {
-            C = p == 1u ? CX : p == 2u ? CY : CZ;
-            Ab = p == 1u ? AX : p == 2u ? AY : AZ;
-        }
-        const float A = Ab * ex2(win[n]);
-        // lambda = ln(C / A); delta = 1 - tanh(|lambda|/2) = 2 min(C, A) / (C + A),
-        // at least delta_clip; or phi(|lambda|) = log1p(2 min(C, A) / |C - A|),
-        // at least phi_clip (|lambda| <= msg_clip)
-        float dl;
-        if (PHI) {
-            const float mx = fmaxf(C, A), mn = fminf(C, A);
-            dl = fmaxf(log1p_rel(2.0f * mn * rcp(mx - mn)), sp.vclip);
-        } else {
-            dl = fmaxf(2.0f * fminf(C, A) * rcp(C + A), sp.vclip);
-        }
         const uint32_t abit = SPLIT ? (n < 2 ? ab & 1u : ab >> 1) : (ab >> (8 * n)) & 1u;
-        const uint32_t bits = (__float_as_uint(dl) & ~1u) | abit | (A > C ? 0x80000000u : 0u);
+        const uint32_t bits = (__float_as_uint(dl[n]) & ~1u) | abit | (A[n] > C[n] ? 0x80000000u : 0u);
         out[n] = (FULL || p) ? __uint_as_float(bits) : 0.f;
         if (TRACE && a.tr_v2c && p) {
-            const float lam = fminf(fmaxf(kLn2 * (lg2(C) - lg2(A)), -a.clip), a.clip);
+            const float lam = fminf(fmaxf(kLn2 * (lg2(C[n]) - lg2(A[n])), -a.clip), a.clip);
             const int s = SPLIT ? n * sp.Np + j : 4 * j + n;
             a.tr_v2c[((size_t)shot * (sp.max_iter + 1) + t) * a.E + a.var_canon[s]] = lam;
         }
@@ -488,12 +512,16 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                         ext[2] = e01 + mag[3];
                         ext[3] = e01 + mag[2];
                     } else {
-                        // extrinsic D of each edge: the (+) of the other three deltas
-                        const float d01 = oplus(mag[0], mag[1]), d23 = oplus(mag[2], mag[3]);
-                        ext[0] = oplus(mag[1], d23);
-                        ext[1] = oplus(mag[0], d23);
-                        ext[2] = oplus(d01, mag[3]);
-                        ext[3] = oplus(d01, mag[2]);
+                        // extrinsic D of each edge: the (+) of the other three deltas,
+                        // two (+) per packed f32x2 instruction pair (each lane equals
+                        // the scalar oplus; a (+) b and b (+) a round alike)
+                        const float2 d = oplus2(make_float2(mag[0], mag[2]), make_float2(mag[1], mag[3]));
+                        const float2 e01 = oplus2(make_float2(mag[1], mag[0]), make_float2(d.y, d.y));
+                        const float2 e23 = oplus2(make_float2(mag[3], mag[2]), make_float2(d.x, d.x));
+                        ext[0] = e01.x;
+                        ext[1] = e01.y;
+                        ext[2] = e23.x;
+                        ext[3] = e23.y;
                     }
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
