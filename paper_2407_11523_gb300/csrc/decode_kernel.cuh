@@ -294,8 +294,25 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &
     const float e0 = ex2(c0);
     const float eX = ex2(c0 - QX), eY = ex2(c0 - QY), eZ = ex2(c0 - QZ);
     // C = 1 + e^{-Q_H} and the two anticommuting terms, for H = X, Y, Z
-    const float CX = e0 + eX, CY = e0 + eY, CZ = e0 + eZ;
-    const float AX = eY + eZ, AY = eX + eZ, AZ = eX + eY;
+    float CX, CY, CZ, AX, AY, AZ;
+    if (FULL) {
+        // (C_X, A_X) and (C_Z, A_Z) in two f32x2 sums; C_Y, A_Y are unused in
+        // the split layout (in the other kernels the pairs cost registers)
+        const float2 cax = __fadd2_rn(make_float2(e0, eY), make_float2(eX, eZ));
+        const float2 caz = __fadd2_rn(make_float2(e0, eX), make_float2(eZ, eY));
+        CX = cax.x;
+        AX = cax.y;
+        CZ = caz.x;
+        AZ = caz.y;
+        CY = AY = 0.f;
+    } else {
+        CX = e0 + eX;
+        CY = e0 + eY;
+        CZ = e0 + eZ;
+        AX = eY + eZ;
+        AY = eX + eZ;
+        AZ = eX + eY;
+    }
     float C[4], Ab[4], x[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
@@ -563,8 +580,9 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                     // 2, 3: Z-type edges (with X and Y); unused slots hold 0
 #pragma unroll
                     for (int n = 0; n < 4; ++n) win[n] = slots[n * Np + j];
-                    S[2] = win[0] + win[1];
-                    S[0] = win[2] + win[3];
+                    const float2 s20 = __fadd2_rn(make_float2(win[0], win[2]), make_float2(win[1], win[3]));
+                    S[2] = s20.x;
+                    S[0] = s20.y;
                     S[1] = S[0] + S[2];
                 } else {
                     const float4 w4 = *reinterpret_cast<const float4 *>(slots + 4 * j);
@@ -576,32 +594,43 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                 }
                 const float Pi[3] = {PiS[j], PiS[Np + j], PiS[2 * Np + j]};
                 float Q[3];
+                if (VARIANT == BPQ_EWAINIT) {
+                    // eq. (EWAInit): the state holds Pi^(t) (Pi^(0) at t = 1), so
+                    // Q^(t) = Pi^(t) + S and Pi^(t+1) = alpha Pi^(0) + (1-alpha) Q^(t);
+                    // Paulis X and Y share one f32x2 pair
+                    const float oma = 1.f - alpha;
+                    const float2 q01 = __fadd2_rn(make_float2(state[j], state[Np + j]), make_float2(S[0], S[1]));
+                    const float2 n01 = __ffma2_rn(make_float2(oma, oma), q01,
+                                                  make_float2(state[3 * Np + j], state[4 * Np + j]));
+                    Q[0] = q01.x;
+                    Q[1] = q01.y;
+                    Q[2] = state[2 * Np + j] + S[2];
+                    state[j] = n01.x;
+                    state[Np + j] = n01.y;
+                    state[2 * Np + j] = fmaf(oma, Q[2], state[5 * Np + j]);
+                } else {
 #pragma unroll
-                for (int w = 0; w < 3; ++w) {
-                    if (VARIANT == BPQ_PLAIN) {
-                        Q[w] = Pi[w] + S[w];  // eq. (p_update)
-                    } else if (VARIANT == BPQ_EWAINIT) {
-                        // eq. (EWAInit): the state holds Pi^(t) (Pi^(0) at t = 1);
-                        // Pi^(t+1) = alpha Pi^(0) + (1-alpha) Q^(t)
-                        Q[w] = state[w * Np + j] + S[w];
-                        state[w * Np + j] = fmaf(1.f - alpha, Q[w], state[(3 + w) * Np + j]);
-                    } else if (VARIANT == BPQ_MOMENTUM) {
-                        // eqs. (mombp1), (mombp2) with the gradient of (mombp3)
-                        const float qp = state[w * Np + j];
-                        const float grad = qp - Pi[w] - S[w];
-                        const float g = sp.gamma * state[(3 + w) * Np + j] + (1.f - sp.gamma) * grad;
-                        Q[w] = qp - sp.alpha * g;
-                        state[w * Np + j] = Q[w];
-                        state[(3 + w) * Np + j] = g;
-                    } else {
-                        // eq. (boost) from t = 2; G accumulates g'^2
-                        const float qp = state[w * Np + j];
-                        const float gp = qp - Pi[w] - S[w];
-                        float Gs = state[(3 + w) * Np + j];
-                        if (t >= 2 || sp.ada_from1) Gs += gp * gp;
-                        Q[w] = t == 1 ? Pi[w] + S[w] : qp - sp.alpha * gp * rcp(sqrt_approx(Gs) + sp.eps);
-                        state[w * Np + j] = Q[w];
-                        state[(3 + w) * Np + j] = Gs;
+                    for (int w = 0; w < 3; ++w) {
+                        if (VARIANT == BPQ_PLAIN) {
+                            Q[w] = Pi[w] + S[w];  // eq. (p_update)
+                        } else if (VARIANT == BPQ_MOMENTUM) {
+                            // eqs. (mombp1), (mombp2) with the gradient of (mombp3)
+                            const float qp = state[w * Np + j];
+                            const float grad = qp - Pi[w] - S[w];
+                            const float g = sp.gamma * state[(3 + w) * Np + j] + (1.f - sp.gamma) * grad;
+                            Q[w] = qp - sp.alpha * g;
+                            state[w * Np + j] = Q[w];
+                            state[(3 + w) * Np + j] = g;
+                        } else {
+                            // eq. (boost) from t = 2; G accumulates g'^2
+                            const float qp = state[w * Np + j];
+                            const float gp = qp - Pi[w] - S[w];
+                            float Gs = state[(3 + w) * Np + j];
+                            if (t >= 2 || sp.ada_from1) Gs += gp * gp;
+                            Q[w] = t == 1 ? Pi[w] + S[w] : qp - sp.alpha * gp * rcp(sqrt_approx(Gs) + sp.eps);
+                            state[w * Np + j] = Q[w];
+                            state[(3 + w) * Np + j] = Gs;
+                        }
                     }
                 }
                 // hard decision: I if all Q_W > 0, else the first minimum of X, Y, Z
