@@ -718,10 +718,11 @@ __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const 
         if (shot >= a.B) break;
         if (VARIANT == BPQ_AEWA) {
             // Appendix C: EWAInit-BP with alpha = 1.0, 0.9, ..., 0.0 in turn until
-            // a run converges (the outputs are those of the last run)
+            // a run converges (the outputs are those of the last run); alpha_k =
+            // (10 - k) / 10 by IEEE division, the float nearest to it
             for (int k = 0; k <= 10; ++k)
                 if (decode_shot<BPQ_EWAINIT, NPT, TRACE, SPLIT, FULL>(a, adj, m, NPT, T, tg, G, bar_id, shot,
-                                                                    1.0f - 0.1f * (float)k))
+                                                                    (float)(10 - k) / 10.0f))
                     break;
         } else {
             decode_shot<VARIANT, NPT, TRACE, SPLIT, FULL>(a, adj, m, NPT, T, tg, G, bar_id, shot, a.alpha);

@@ -464,6 +464,33 @@ def test_aewa_planar_matches_oracle(bpq, L):
     assert (fail_g[conv == 1] != 1).all() and (fail_g[conv == 0] == 1).all()
 
 
+@pytest.mark.parametrize("kind,d", [("planar", 7), ("toric", 6)])
+def test_aewa_equals_its_ewainit_runs(bpq, kind, d):
+    """AEWA-BP is EWAInit-BP retried with alpha = 1.0, 0.9, ..., 0.0 (the
+    float nearest (10 - k) / 10): per shot, its outputs equal bit for bit those
+    of the first of eleven EWAInit-BP decodes that converges, else those of
+    the alpha = 0 decode, marked not converged.  Toric codes run the kernels
+    for codes without padding."""
+    t = bpq.Tanner(kind, d)
+    ch = oracle.depolarizing(0.08)
+    _, syn = bpq.sample(t, *ch, seed=0xAE3A0100 + d, shot0=0, B=3000)
+    prior = bpq.prior_tensor(t, *ch)
+    est, conv, iters = (x.cpu().numpy() for x in bpq.decode(t, syn, prior, "aewa", max_iter=40))
+    runs = []
+    for k in range(11):
+        alpha = float(np.float32(10 - k) / np.float32(10))
+        runs.append([x.cpu().numpy() for x in bpq.decode(t, syn, prior, "ewainit", max_iter=40, alpha=alpha)])
+    conv_k = np.stack([r[1] for r in runs])  # (11, B)
+    first = np.where(conv_k.any(axis=0), conv_k.argmax(axis=0), 10)
+    b = np.arange(syn.shape[0])
+    est_c = np.stack([r[0] for r in runs])[first, b]
+    iters_c = np.stack([r[2] for r in runs])[first, b]
+    assert np.array_equal(est, est_c)
+    assert np.array_equal(conv.astype(bool), conv_k.any(axis=0))
+    assert np.array_equal(iters, iters_c)
+    assert (first > 0).sum() > 0 and conv.mean() > conv_k[0].mean()
+
+
 def test_aewa_host_path_and_refusals(bpq):
     """AEWA-BP through the host-buffer entry point equals the device one; the
     trace and batched entry points refuse it with an error, not a launch."""
