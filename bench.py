@@ -82,6 +82,17 @@ def workload_config(args):
     }
 
 
+def kernel_code_hash(src: str) -> str:
+    """First 16 hex digits of the SHA-256 of a CUDA source with its comments
+    and all whitespace removed: it changes when the code does, not when a
+    comment does."""
+    import hashlib
+    import re
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return hashlib.sha256("".join(src.split()).encode()).hexdigest()[:16]
+
+
 # ------------------------------------------------------------------ dist
 
 def dist_setup(args):
@@ -375,16 +386,16 @@ def run_ours(args, rank, world):
 
     # roofline of the decode kernel: SFU-bound in-SM arithmetic.  DRAM traffic
     # per shot comes from the committed ncu summary, used only while the
-    # kernel source still matches the profiled one.
+    # kernel's code (comments and whitespace aside) still matches the
+    # profiled one.
     traffic = issue_pct = None
     try:
-        import hashlib
         prof = open(os.path.join(ROOT, "profiles", "decode_kernel_toric15_ewainit.md")).read()
-        src = open(os.path.join(ROOT, "paper_2407_11523_gb300", "csrc", "decode_kernel.cuh"), "rb").read()
-        want = [ln.split(":")[1].strip() for ln in prof.splitlines() if ln.startswith("kernel_source_sha256_16:")][0]
+        src = open(os.path.join(ROOT, "paper_2407_11523_gb300", "csrc", "decode_kernel.cuh")).read()
+        want = [ln.split(":")[1].split()[0] for ln in prof.splitlines() if ln.startswith("kernel_code_sha256_16:")][0]
         per_shot = float([ln for ln in prof.splitlines() if "traffic_bytes_per_shot:" in ln][0]
                          .split("traffic_bytes_per_shot:")[1].split()[0])
-        if hashlib.sha256(src).hexdigest()[:16] == want:
+        if kernel_code_hash(src) == want:
             traffic = per_shot * args.shots_per_p
             issue_pct = float([ln for ln in prof.splitlines() if "issue_active_pct:" in ln][0]
                               .split("issue_active_pct:")[1].split()[0])

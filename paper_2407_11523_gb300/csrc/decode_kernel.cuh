@@ -19,7 +19,7 @@
 //    pass XORs sign bits and forms D = 1 - prod_k (1 - delta_k) with
 //    a (+) b = a + b - ab (no relative accuracy is lost for small deltas,
 //    i.e. confident messages), then |m_c->v| = 2 atanh(1 - D) =
-//    ln((2 - D) / D): one reciprocal and one logarithm per edge.  AdaGrad-BP
+//    ln(2/D - 1): one reciprocal, one fma and one logarithm per edge.  AdaGrad-BP
 //    keeps Gallager's sign/phi form (see PhiForm) for its conditioning.
 //  * variable-to-check, eqs. (lambda), (v_update), (mombp5): the message is
 //    lambda_H(Q - own anticommuting message) = ln(C / A) with
@@ -36,6 +36,14 @@
 //    scale factor.  The decisions are unchanged (a positive scale), the EWA
 //    and momentum recursions are linear, AdaGrad's alpha and eps are scaled
 //    by log2 e on the host, and the trace reports natural-log values.
+//  * pairs: independent fp32 adds, multiplies and fmas of two edges (or two
+//    sums) go through one packed f32x2 instruction (__fadd2_rn, __fmul2_rn,
+//    __ffma2_rn), each lane rounded as the scalar operation.
+//
+// Specialisations: SPLIT (tables whose qubits have at most two X and two Z
+// edges: the edge type is fixed by its position, so no per-edge Pauli
+// selects) and FULL (split tables without padding, e.g. the toric codes: no
+// zero/trash slot choice, no unused positions, no check-side clip).
 #pragma once
 
 #include <cuda_runtime.h>
