@@ -340,11 +340,15 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &
     // Edges n, n+1 share packed two-lane fp32 instructions (f32x2): each lane
     // rounds as the scalar operation would.
     float A[4], dl[4];
+    uint32_t neg[4];  // sign bit of C - A: set iff A > C, i.e. lambda < 0 (C = A gives +0)
 #pragma unroll
     for (int n = 0; n < 4; n += 2) {
         const float2 A2 = __fmul2_rn(make_float2(Ab[n], Ab[n + 1]), make_float2(x[n], x[n + 1]));
         A[n] = A2.x;
         A[n + 1] = A2.y;
+        const float2 cma = __fadd2_rn(make_float2(C[n], C[n + 1]), make_float2(-A2.x, -A2.y));
+        neg[n] = __float_as_uint(cma.x) & 0x80000000u;
+        neg[n + 1] = __float_as_uint(cma.y) & 0x80000000u;
         if (PHI) {
 #pragma unroll
             for (int h = n; h < n + 2; ++h) {
@@ -365,7 +369,7 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &
     for (int n = 0; n < 4; ++n) {
         const uint32_t p = (vp >> (2 * n)) & 3u;
         const uint32_t abit = SPLIT ? (n < 2 ? ab & 1u : ab >> 1) : (ab >> (8 * n)) & 1u;
-        const uint32_t bits = (__float_as_uint(dl[n]) & ~1u) | abit | (A[n] > C[n] ? 0x80000000u : 0u);
+        const uint32_t bits = (__float_as_uint(dl[n]) & ~1u) | abit | neg[n];
         out[n] = (FULL || p) ? __uint_as_float(bits) : 0.f;
         if (TRACE && a.tr_v2c && p) {
             const float lam = fminf(fmaxf(kLn2 * (lg2(C[n]) - lg2(A[n])), -a.clip), a.clip);
