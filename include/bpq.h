@@ -106,6 +106,14 @@ int bpq_tanner_upload(bpq_tanner *t, int device);
  * qubits (-1 if unknown).  Any output pointer may be NULL. */
 int bpq_tanner_info(const bpq_tanner *t, int *N, int *M, int *E, int *K);
 
+/* The message layout the decode kernels use for this graph (host only, no
+ * GPU needed): 0 generic (slots by check order, per-edge Pauli selects);
+ * 1 split (no Y entries and at most two X and two Z edges per qubit: the
+ * edge's Pauli is fixed by its slot); 2 split without padding (every check
+ * of degree 4 and every qubit with two X and two Z edges, e.g. the toric
+ * codes).  Results do not depend on the layout.  Errors: EINVAL (NULL). */
+int bpq_tanner_layout(const bpq_tanner *t, int *layout);
+
 /* Check-major CSR of the graph on the host: chk_ptr[M+1], chk_var[E],
  * pauli[E]; edges of check i are chk_ptr[i] .. chk_ptr[i+1]-1 in increasing
  * qubit order.  This is also the edge order of bpq_decode_trace. */

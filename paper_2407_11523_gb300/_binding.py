@@ -52,6 +52,7 @@ def lib():
             "bpq_tanner_set_logicals": (i, [P, i, P]),
             "bpq_tanner_upload": (i, [P, i]),
             "bpq_tanner_info": (i, [P, pi, pi, pi, pi]),
+            "bpq_tanner_layout": (i, [P, pi]),
             "bpq_tanner_export": (i, [P, P, P, P]),
             "bpq_tanner_logicals": (i, [P, P]),
             "bpq_free_tanner": (None, [P]),
@@ -196,6 +197,13 @@ class Tanner:
         L = np.zeros((2 * max(self.K, 0), self.N), dtype=np.uint8)
         _check(lib().bpq_tanner_logicals(self._h, _ptr(L)), "bpq_tanner_logicals")
         return L
+
+    def layout(self) -> int:
+        """The decode kernels' message layout: 0 generic, 1 split, 2 split
+        without padding (bpq_tanner_layout)."""
+        v = ctypes.c_int()
+        _check(lib().bpq_tanner_layout(self._h, ctypes.byref(v)), "bpq_tanner_layout")
+        return v.value
 
     def set_launch(self, threads_per_shot=0, shots_per_cta=0):
         _check(lib().bpq_set_launch(self._h, threads_per_shot, shots_per_cta), "bpq_set_launch")

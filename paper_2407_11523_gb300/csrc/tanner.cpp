@@ -345,6 +345,12 @@ int bpq_tanner_info(const bpq_tanner *t, int *N, int *M, int *E, int *K) {
     return BPQ_OK;
 }
 
+int bpq_tanner_layout(const bpq_tanner *t, int *layout) {
+    if (!t || !layout) return fail(BPQ_EINVAL, "NULL argument");
+    *layout = t->full ? 2 : t->split ? 1 : 0;
+    return BPQ_OK;
+}
+
 int bpq_tanner_export(const bpq_tanner *t, int32_t *chk_ptr, int32_t *chk_var, uint8_t *pauli) {
     if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
     if (chk_ptr) std::memcpy(chk_ptr, t->chk_ptr.data(), sizeof(int32_t) * (t->M + 1));

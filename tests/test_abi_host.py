@@ -133,3 +133,25 @@ def test_prior_rows_match_the_shared_input_generator(bpq):
     assert np.abs(r).max() <= 2.0 ** -16 + 2.0 ** -23 and np.unique(a[:, 0]).size > 300  # float32 resolves about 330 levels here
     assert (a[:, 0] == a[:, 1]).all() and (a[:, 1] == a[:, 2]).all()
     assert np.array_equal(bpq.prior_rows(9, 0.01, 0.02, 0.03), np.tile(np.float32([0.01, 0.02, 0.03]), (9, 1)))
+
+
+def test_message_layout_of_each_code_family(bpq):
+    """Toric codes have no padding slots (every check of degree 4, every
+    qubit two X and two Z edges); planar and XZZX codes use the split layout
+    with padding; a Y entry, or three edges of one type on a qubit, forces the
+    generic layout."""
+    for d in (3, 6, 15):
+        assert bpq.Tanner("toric", d).layout() == 2
+    for kind in ("planar", "xzzx"):
+        for d in (3, 7):
+            assert bpq.Tanner(kind, d).layout() == 1
+    H = bpq.Tanner("toric", 5).dense()
+    Hy = H.copy()
+    Hy[0, np.nonzero(H[0])[0][0]] = 2  # one Y entry
+    assert bpq.Tanner(H=Hy).layout() == 0
+    Hx = np.concatenate([H, np.zeros((H.shape[0], 1), dtype=np.uint8)], axis=1)  # an isolated qubit
+    assert bpq.Tanner(H=Hx).layout() == 1
+    assert bpq.Tanner(H=random_tree_code(10, seed=3)).layout() in (0, 1)
+    T = np.zeros((3, 1), dtype=np.uint8)
+    T[:, 0] = 1  # one qubit on three X checks
+    assert bpq.Tanner(H=T).layout() == 0
