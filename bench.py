@@ -10,8 +10,10 @@ than the 129 MB L2, so no flush is needed between steps).
 Reported: shots/s and edge-updates/s of EWAInit-BP (the headline) and of
 plain/Momentum/AdaGrad BP on the same inputs, p50/p99 launch latency,
 the roofline of the decode kernel, an end-to-end figure through the C-ABI
-host-buffer entry point (bpq_decode_host), and the FP64 oracle timed on the
-host cores as a CPU baseline.
+host-buffer entry point (bpq_decode_host), the FP64 oracle timed on the
+host cores as a CPU baseline, and the logical error rate per p on the
+uniform priors and (untimed) on priors with a 2^-16 per-qubit jitter, which
+breaks the exact symmetric ties that uniform priors leave on the torus.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank decodes its own Philox shot range (weak scaling).
