@@ -9,6 +9,12 @@ The arithmetic lives in ``bp_oracle.c`` (decoder) and ``noise_oracle.c``
 (sampler), compiled with gcc into ``_oracle.so`` beside them; this module only
 marshals numpy arrays.  Code construction and GF(2) tools are in
 ``codes.py``.
+
+``decode`` and ``trace`` take ``precision``: "f64" (the oracle proper,
+double precision), "ext" (the same source computing in long double) or
+"f32" (double arithmetic with every stored message, posterior, prior and
+state value rounded to binary32).  The two other builds exist to show which
+results the working precision decides; parity is measured against "f64".
 """
 from __future__ import annotations
 
@@ -21,8 +27,14 @@ import numpy as np
 from . import codes  # noqa: F401  (re-export)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SO = os.path.join(_HERE, "_oracle.so")
 _SOURCES = [os.path.join(_HERE, f) for f in ("bp_oracle.c", "noise_oracle.c")]
+# precision -> (shared object, extra gcc flags); only the f64 build carries the sampler
+_BUILDS = {
+    "f64": (os.path.join(_HERE, "_oracle.so"), [], _SOURCES),
+    "ext": (os.path.join(_HERE, "_oracle_ext.so"), ["-DORACLE_REAL=long double"], _SOURCES[:1]),
+    "f32": (os.path.join(_HERE, "_oracle_f32.so"), ["-DORACLE_STORE_F32"], _SOURCES[:1]),
+}
+_SO = _BUILDS["f64"][0]
 
 PLAIN, MOMENTUM, ADAGRAD, EWAINIT, AEWA = 0, 1, 2, 3, 4
 VARIANTS = {"plain": PLAIN, "momentum": MOMENTUM, "adagrad": ADAGRAD, "ewainit": EWAINIT, "aewa": AEWA}
@@ -38,41 +50,48 @@ DEFAULT_PARAMS = {
 }
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle's C sources into _oracle.so (plain gcc -O2)."""
+def build(force: bool = False, precision: str | None = None) -> str:
+    """Compile the oracle's C sources (plain gcc -O2): _oracle.so, and the
+    extended-precision and binary32-storage builds of the decoder.  With
+    `precision`, only that build."""
     newest = max(os.path.getmtime(s) for s in _SOURCES)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
-        tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, *_SOURCES, "-lm", "-lpthread"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
+    for prec, (so, flags, srcs) in _BUILDS.items():
+        if precision is not None and prec != precision:
+            continue
+        if force or not os.path.exists(so) or os.path.getmtime(so) < newest:
+            tmp = so + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *flags, "-o", tmp, *srcs, "-lm", "-lpthread"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, so)
     return _SO
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = ctypes.CDLL(_SO)
+def lib(precision: str = "f64"):
+    if precision not in _BUILDS:
+        raise ValueError(f"precision must be one of {sorted(_BUILDS)}")
+    if precision not in _libs:
+        build(precision=precision)
+        L = ctypes.CDLL(_BUILDS[precision][0])
         P = ctypes.c_void_p
         i, d, u64 = ctypes.c_int, ctypes.c_double, ctypes.c_uint64
         L.oracle_decode.argtypes = [i, i, P, i, P, P, i, d, d, d, d, i, i, i, P, P, P, i]
         L.oracle_decode.restype = i
         L.oracle_trace.argtypes = [i, i, P, P, P, i, d, d, d, d, i, i, i, P, P, P, P, P, P]
         L.oracle_trace.restype = i
-        L.oracle_sample.argtypes = [i, i, P, d, d, d, u64, u64, i, P, P]
-        L.oracle_sample.restype = i
-        L.oracle_philox4x64_10.argtypes = [P, P, P]
-        L.oracle_philox4x64_10.restype = None
+        if precision == "f64":
+            L.oracle_sample.argtypes = [i, i, P, d, d, d, u64, u64, i, P, P]
+            L.oracle_sample.restype = i
+            L.oracle_philox4x64_10.argtypes = [P, P, P]
+            L.oracle_philox4x64_10.restype = None
         L.oracle_num_edges.argtypes = [i, i, P]
         L.oracle_num_edges.restype = i
         L.oracle_hard_decision.argtypes = [P]
         L.oracle_hard_decision.restype = i
-        _lib = L
-    return _lib
+        _libs[precision] = L
+    return _libs[precision]
 
 
 def _ptr(a: np.ndarray):
@@ -113,10 +132,11 @@ SCHEDULES = {"parallel": 0, "serial": 1}
 
 
 def decode(H, syn, prior, variant=PLAIN, max_iter=50, alpha=None, gamma=None, eps=None,
-           msg_clip=None, adagrad_g_from_iter1=None, nthreads=1, schedule="parallel"):
+           msg_clip=None, adagrad_g_from_iter1=None, nthreads=1, schedule="parallel", precision="f64"):
     """Decode B syndromes. syn: (B, M) 0/1; prior: (N, 3) probabilities
     (p^X, p^Y, p^Z).  schedule: "parallel" (flooding) or "serial"
-    (Algorithm 1's qubit-by-qubit sweep).  Returns (est (B,N) codes,
+    (Algorithm 1's qubit-by-qubit sweep).  precision: "f64", "ext" or
+    "f32" (see the module docstring).  Returns (est (B,N) codes,
     conv (B,) bool, iters (B,))."""
     H = np.ascontiguousarray(H, dtype=np.uint8)
     M, N = H.shape
@@ -128,7 +148,7 @@ def decode(H, syn, prior, variant=PLAIN, max_iter=50, alpha=None, gamma=None, ep
     conv = np.zeros(B, dtype=np.uint8)
     iters = np.zeros(B, dtype=np.int32)
     a, g, e, c, f = _params(variant, alpha, gamma, eps, msg_clip, adagrad_g_from_iter1)
-    rc = lib().oracle_decode(N, M, _ptr(H), B, _ptr(syn), _ptr(prior), variant, a, g, e, c, f,
+    rc = lib(precision).oracle_decode(N, M, _ptr(H), B, _ptr(syn), _ptr(prior), variant, a, g, e, c, f,
                              SCHEDULES[schedule], max_iter, _ptr(est), _ptr(conv), _ptr(iters), nthreads)
     if rc:
         raise ValueError(f"oracle_decode failed ({rc})")
@@ -136,7 +156,7 @@ def decode(H, syn, prior, variant=PLAIN, max_iter=50, alpha=None, gamma=None, ep
 
 
 def trace(H, syn, prior, variant=PLAIN, T=5, alpha=None, gamma=None, eps=None, msg_clip=None,
-          adagrad_g_from_iter1=None, schedule="parallel"):
+          adagrad_g_from_iter1=None, schedule="parallel", precision="f64"):
     """Run exactly T iterations on one syndrome and return every intermediate
     quantity: dict with m_v2c (T+1, E), m_c2v (T, E), S, Q, aux (T, N, 3) and
     dec (T, N).  Edges are in check-major order (row i of H, columns j
@@ -150,7 +170,7 @@ def trace(H, syn, prior, variant=PLAIN, T=5, alpha=None, gamma=None, eps=None, m
     out = dict(m_v2c=np.zeros((T + 1, E)), m_c2v=np.zeros((T, E)), S=np.zeros((T, N, 3)),
                Q=np.zeros((T, N, 3)), aux=np.zeros((T, N, 3)), dec=np.zeros((T, N), dtype=np.uint8))
     a, g, e, c, f = _params(variant, alpha, gamma, eps, msg_clip, adagrad_g_from_iter1)
-    rc = lib().oracle_trace(N, M, _ptr(H), _ptr(syn), _ptr(prior), variant, a, g, e, c, f,
+    rc = lib(precision).oracle_trace(N, M, _ptr(H), _ptr(syn), _ptr(prior), variant, a, g, e, c, f,
                             SCHEDULES[schedule], T,
                             _ptr(out["m_v2c"]), _ptr(out["m_c2v"]), _ptr(out["S"]), _ptr(out["Q"]),
                             _ptr(out["aux"]), _ptr(out["dec"]))

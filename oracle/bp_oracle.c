@@ -51,21 +51,45 @@
  *   - The horizontal update is evaluated in long double so that the
  *     literal tanh/atanh form keeps its accuracy near the clip value.
  *
+ * Working precision.  The default build computes in double (FP64).  Two
+ * other builds of this same file serve one purpose: to show which results
+ * the working precision decides.  -DORACLE_REAL="long double" computes every
+ * quantity in long double (x87 80-bit on x86-64, IEEE binary128 on AArch64);
+ * -DORACLE_STORE_F32 keeps double arithmetic but rounds every stored
+ * message, posterior, prior and state value (and every partial sum) to
+ * binary32, the precision in which a single-precision decoder keeps them.
+ * The update rules are the same in all three builds.
+ *
  * Pauli codes used throughout: 0 = I, 1 = X, 2 = Y, 3 = Z.  W indexes
  * {X, Y, Z} as 0, 1, 2 (code W+1).
  */
-#include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
+
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+
+/* A value as the decoder stores it: unchanged, or rounded to binary32 in the
+ * ORACLE_STORE_F32 build. */
+static real st(real x) {
+#ifdef ORACLE_STORE_F32
+    return (real)(float)x;
+#else
+    return x;
+#endif
+}
 
 enum { OR_PLAIN = 0, OR_MOMENTUM = 1, OR_ADAGRAD = 2, OR_EWAINIT = 3, OR_AEWA = 4 };
 
 /* Trace-product <A, B>: 1 when the single-qubit Paulis anticommute. */
 static int anticommutes(int a, int b) { return a != 0 && b != 0 && a != b; }
 
-static double clip(double x, double c) {
+static real clip(real x, real c) {
     if (x > c) return c;
     if (x < -c) return -c;
     return x;
@@ -75,9 +99,9 @@ static double clip(double x, double c) {
  * eq. (lambda).  The denominator is the sum over the two Paulis W != H, which
  * is what the printed difference equals; summing them directly avoids the
  * cancellation of the printed form. */
-static double lambda_fn(int h, const double q[3]) {
-    double num = 1.0 + exp(-q[h - 1]);
-    double den = 0.0;
+static real lambda_fn(int h, const real q[3]) {
+    real num = 1.0 + exp(-q[h - 1]);
+    real den = 0.0;
     for (int w = 0; w < 3; ++w)
         if (w != h - 1) den += exp(-q[w]);
     return log(num / den);
@@ -136,7 +160,7 @@ static void graph_free(graph *g) {
 }
 
 typedef struct {
-    double alpha, gamma, eps, msg_clip;
+    real alpha, gamma, eps, msg_clip;
     int adagrad_g_from_iter1;
     int serial;  /* 0: parallel (flooding) schedule; 1: serial schedule of Algorithm 1 */
 } params;
@@ -151,22 +175,27 @@ typedef struct {
     uint8_t *dec;    /* T x N     : hard decisions */
 } trace;
 
+/* Copy n working-precision values into a caller's double array. */
+static void put(double *dst, const real *src, size_t n) {
+    for (size_t k = 0; k < n; ++k) dst[k] = (double)src[k];
+}
+
 typedef struct {
-    double *Pi0, *Pit, *Q, *Qprev, *S, *gstate;
-    double *m_v2c, *m_c2v;
+    real *Pi0, *Pit, *Q, *Qprev, *S, *gstate;
+    real *m_v2c, *m_c2v;
     uint8_t *est;
 } workspace;
 
 static int ws_alloc(workspace *w, int N, int E) {
     size_t n3 = (size_t)3 * N;
-    w->Pi0 = malloc(sizeof(double) * n3);
-    w->Pit = malloc(sizeof(double) * n3);
-    w->Q = malloc(sizeof(double) * n3);
-    w->Qprev = malloc(sizeof(double) * n3);
-    w->S = malloc(sizeof(double) * n3);
-    w->gstate = malloc(sizeof(double) * n3);
-    w->m_v2c = malloc(sizeof(double) * (E + 1));
-    w->m_c2v = malloc(sizeof(double) * (E + 1));
+    w->Pi0 = malloc(sizeof(real) * n3);
+    w->Pit = malloc(sizeof(real) * n3);
+    w->Q = malloc(sizeof(real) * n3);
+    w->Qprev = malloc(sizeof(real) * n3);
+    w->S = malloc(sizeof(real) * n3);
+    w->gstate = malloc(sizeof(real) * n3);
+    w->m_v2c = malloc(sizeof(real) * (E + 1));
+    w->m_c2v = malloc(sizeof(real) * (E + 1));
     w->est = malloc(N + 1);
     return (w->Pi0 && w->Pit && w->Q && w->Qprev && w->S && w->gstate && w->m_v2c &&
             w->m_c2v && w->est) ? 0 : -1;
@@ -179,7 +208,7 @@ static void ws_free(workspace *w) {
 
 /* Hard decision of Sec. II-B1: I if every Q_W > 0, else the W with the
  * smallest Q_W (first minimum in X, Y, Z order). Returns the Pauli code. */
-static int hard_decision(const double q[3]) {
+static int hard_decision(const real q[3]) {
     if (q[0] > 0 && q[1] > 0 && q[2] > 0) return 0;
     int best = 0;
     for (int w = 1; w < 3; ++w)
@@ -200,34 +229,34 @@ static int syndrome_matches(const graph *g, const uint8_t *est, const uint8_t *s
 
 /* m_{c_i -> v_j} of edge e (check i) from the current v->c messages of the
  * other edges of check i, eq. (h_update) with the syndrome sign, clipped. */
-static double c2v_edge(const graph *g, const workspace *w, const uint8_t *syn, int e, double c) {
+static real c2v_edge(const graph *g, const workspace *w, const uint8_t *syn, int e, real c) {
     const int i = g->edge_chk[e];
     long double prod = 1.0L;
     for (int f = g->chk_ptr[i]; f < g->chk_ptr[i + 1]; ++f)
         if (f != e) prod *= tanhl((long double)w->m_v2c[f] / 2.0L);
     long double wv = 2.0L * atanhl(prod);
-    double m = (syn[i] & 1) ? -(double)wv : (double)wv;
-    return clip(m, c);
+    real m = (syn[i] & 1) ? -(real)wv : (real)wv;
+    return st(clip(m, c));
 }
 
 /* Posterior of one qubit-Pauli pair k = 3j + W for each variant, from the
  * sum S of its anticommuting c->v messages (the rules of Sec. II-B1 and
  * Sec. III, identical under both schedules). */
-static int posterior(int variant, const params *pr, int t, workspace *w, int k, double S) {
-    double Pi = w->Pi0[k], Qp = w->Qprev[k];
+static int posterior(int variant, const params *pr, int t, workspace *w, int k, real S) {
+    real Pi = w->Pi0[k], Qp = w->Qprev[k];
     switch (variant) {
-    case OR_PLAIN: w->Q[k] = Pi + S; return 0;
-    case OR_EWAINIT: w->Q[k] = w->Pit[k] + S; return 0;
+    case OR_PLAIN: w->Q[k] = st(Pi + S); return 0;
+    case OR_EWAINIT: w->Q[k] = st(w->Pit[k] + S); return 0;
     case OR_MOMENTUM: {
-        double grad = Qp - Pi - S;
-        w->gstate[k] = pr->gamma * w->gstate[k] + (1.0 - pr->gamma) * grad;
-        w->Q[k] = Qp - pr->alpha * w->gstate[k];
+        real grad = st(Qp - Pi - S);
+        w->gstate[k] = st(pr->gamma * w->gstate[k] + (1.0 - pr->gamma) * grad);
+        w->Q[k] = st(Qp - pr->alpha * w->gstate[k]);
         return 0;
     }
     case OR_ADAGRAD: {
-        double gp = Qp - Pi - S;
-        if (t >= 2 || pr->adagrad_g_from_iter1) w->gstate[k] += gp * gp;
-        w->Q[k] = t == 1 ? Pi + S : Qp - pr->alpha * gp / (sqrt(w->gstate[k]) + pr->eps);
+        real gp = st(Qp - Pi - S);
+        if (t >= 2 || pr->adagrad_g_from_iter1) w->gstate[k] = st(w->gstate[k] + gp * gp);
+        w->Q[k] = st(t == 1 ? Pi + S : Qp - pr->alpha * gp / (sqrt(w->gstate[k]) + pr->eps));
         return 0;
     }
     }
@@ -242,41 +271,41 @@ static int posterior(int variant, const params *pr, int t, workspace *w, int k, 
  * for t > 1), and sends its new v->c messages: eq. (v_update) for plain and
  * EWAInit BP, eq. (mombp5) for Momentum and AdaGrad BP. */
 static int serial_sweep(const graph *g, const uint8_t *syn, int variant, const params *pr, int t, workspace *w) {
-    const double c = pr->msg_clip;
+    const real c = pr->msg_clip;
     for (int j = 0; j < g->N; ++j) {
         if (variant == OR_EWAINIT && t > 1)
             for (int k = 0; k < 3; ++k)
-                w->Pit[3 * j + k] = pr->alpha * w->Pi0[3 * j + k] + (1.0 - pr->alpha) * w->Qprev[3 * j + k];
+                w->Pit[3 * j + k] = st(pr->alpha * w->Pi0[3 * j + k] + (1.0 - pr->alpha) * w->Qprev[3 * j + k]);
         for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
             const int e = g->var_edges[a];
             w->m_c2v[e] = c2v_edge(g, w, syn, e, c);
         }
         for (int k = 0; k < 3; ++k) {
-            double s = 0.0;
+            real s = 0.0;
             for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
                 const int e = g->var_edges[a];
-                if (anticommutes(k + 1, g->edge_p[e])) s += w->m_c2v[e];
+                if (anticommutes(k + 1, g->edge_p[e])) s = st(s + w->m_c2v[e]);
             }
             w->S[3 * j + k] = s;
             if (posterior(variant, pr, t, w, 3 * j + k, s)) return -1;
         }
         for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
             const int e = g->var_edges[a], h = g->edge_p[e];
-            double q[3];
+            real q[3];
             for (int k = 0; k < 3; ++k) {
                 if (variant == OR_PLAIN || variant == OR_EWAINIT) {
-                    const double *base = (variant == OR_EWAINIT) ? &w->Pit[3 * j] : &w->Pi0[3 * j];
-                    double s = 0.0;
+                    const real *base = (variant == OR_EWAINIT) ? &w->Pit[3 * j] : &w->Pi0[3 * j];
+                    real s = 0.0;
                     for (int b = g->var_ptr[j]; b < g->var_ptr[j + 1]; ++b) {
                         const int f = g->var_edges[b];
-                        if (f != e && anticommutes(k + 1, g->edge_p[f])) s += w->m_c2v[f];
+                        if (f != e && anticommutes(k + 1, g->edge_p[f])) s = st(s + w->m_c2v[f]);
                     }
-                    q[k] = base[k] + s;
+                    q[k] = st(base[k] + s);
                 } else {
-                    q[k] = w->Q[3 * j + k] - (anticommutes(k + 1, h) ? w->m_c2v[e] : 0.0);
+                    q[k] = st(w->Q[3 * j + k] - (anticommutes(k + 1, h) ? w->m_c2v[e] : 0.0));
                 }
             }
-            w->m_v2c[e] = clip(lambda_fn(h, q), c);
+            w->m_v2c[e] = st(clip(lambda_fn(h, q), c));
         }
     }
     return 0;
@@ -289,17 +318,17 @@ static int decode_shot(const graph *g, const uint8_t *syn, const double *prior, 
                        const params *pr, int max_iter, int stop_early, workspace *w,
                        uint8_t *est_out, int *converged, trace *tr) {
     const int N = g->N, E = g->E;
-    const double c = pr->msg_clip;
+    const real c = pr->msg_clip;
 
     /* Prior LLRs Pi^(0)_{v_j,W} = ln(p^I / p^W). */
     for (int j = 0; j < N; ++j) {
-        double pI = 1.0 - prior[3 * j] - prior[3 * j + 1] - prior[3 * j + 2];
-        for (int k = 0; k < 3; ++k) w->Pi0[3 * j + k] = log(pI / prior[3 * j + k]);
+        real pI = 1.0 - (real)prior[3 * j] - (real)prior[3 * j + 1] - (real)prior[3 * j + 2];
+        for (int k = 0; k < 3; ++k) w->Pi0[3 * j + k] = st(log(pI / (real)prior[3 * j + k]));
     }
     /* Initial messages, eq. (init). */
     for (int e = 0; e < E; ++e)
-        w->m_v2c[e] = clip(lambda_fn(g->edge_p[e], &w->Pi0[3 * g->edge_var[e]]), c);
-    if (tr && tr->m_v2c) memcpy(tr->m_v2c, w->m_v2c, sizeof(double) * E);
+        w->m_v2c[e] = st(clip(lambda_fn(g->edge_p[e], &w->Pi0[3 * g->edge_var[e]]), c));
+    if (tr && tr->m_v2c) put(tr->m_v2c, w->m_v2c, E);
 
     /* Q^(0) = Pi^(0) and g^(0) = 0 (Algorithm 1 initialization); G^(0) = 0. */
     for (int k = 0; k < 3 * N; ++k) {
@@ -317,7 +346,7 @@ static int decode_shot(const graph *g, const uint8_t *syn, const double *prior, 
         /* EWAInit-BP: Pi^(t) = alpha Pi^(0) + (1 - alpha) Q^(t-1) when t > 1, eq. (EWAInit). */
         if (variant == OR_EWAINIT && t > 1)
             for (int k = 0; k < 3 * N; ++k)
-                w->Pit[k] = pr->alpha * w->Pi0[k] + (1.0 - pr->alpha) * w->Qprev[k];
+                w->Pit[k] = st(pr->alpha * w->Pi0[k] + (1.0 - pr->alpha) * w->Qprev[k]);
 
         /* Horizontal update, eq. (h_update) and the syndrome sign. */
         for (int i = 0; i < g->M; ++i) {
@@ -326,45 +355,45 @@ static int decode_shot(const graph *g, const uint8_t *syn, const double *prior, 
                 for (int f = g->chk_ptr[i]; f < g->chk_ptr[i + 1]; ++f)
                     if (f != e) prod *= tanhl((long double)w->m_v2c[f] / 2.0L);
                 long double wv = 2.0L * atanhl(prod);
-                double m = (syn[i] & 1) ? -(double)wv : (double)wv;
-                w->m_c2v[e] = clip(m, c);
+                real m = (syn[i] & 1) ? -(real)wv : (real)wv;
+                w->m_c2v[e] = st(clip(m, c));
             }
         }
 
         /* Sum of the c->v messages from checks that anticommute with W. */
         for (int j = 0; j < N; ++j)
             for (int k = 0; k < 3; ++k) {
-                double s = 0.0;
+                real s = 0.0;
                 for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
                     int e = g->var_edges[a];
-                    if (anticommutes(k + 1, g->edge_p[e])) s += w->m_c2v[e];
+                    if (anticommutes(k + 1, g->edge_p[e])) s = st(s + w->m_c2v[e]);
                 }
                 w->S[3 * j + k] = s;
             }
 
         /* Posterior update of each variant. */
         for (int k = 0; k < 3 * N; ++k) {
-            double Pi = w->Pi0[k], S = w->S[k], Qp = w->Qprev[k];
+            real Pi = w->Pi0[k], S = w->S[k], Qp = w->Qprev[k];
             switch (variant) {
             case OR_PLAIN: /* eq. (p_update) */
-                w->Q[k] = Pi + S;
+                w->Q[k] = st(Pi + S);
                 break;
             case OR_EWAINIT: /* eq. (p_update) with Pi replaced by Pi^(t), Algorithm 2 */
-                w->Q[k] = w->Pit[k] + S;
+                w->Q[k] = st(w->Pit[k] + S);
                 break;
             case OR_MOMENTUM: { /* eqs. (mombp1), (mombp2); the gradient as expanded in (mombp3) */
-                double grad = Qp - Pi - S;
-                w->gstate[k] = pr->gamma * w->gstate[k] + (1.0 - pr->gamma) * grad;
-                w->Q[k] = Qp - pr->alpha * w->gstate[k];
+                real grad = st(Qp - Pi - S);
+                w->gstate[k] = st(pr->gamma * w->gstate[k] + (1.0 - pr->gamma) * grad);
+                w->Q[k] = st(Qp - pr->alpha * w->gstate[k]);
                 break;
             }
             case OR_ADAGRAD: { /* eq. (boost) with g' and G as defined below it */
-                double gp = Qp - Pi - S;
-                if (t >= 2 || pr->adagrad_g_from_iter1) w->gstate[k] += gp * gp;
+                real gp = st(Qp - Pi - S);
+                if (t >= 2 || pr->adagrad_g_from_iter1) w->gstate[k] = st(w->gstate[k] + gp * gp);
                 if (t == 1)
-                    w->Q[k] = Pi + S;
+                    w->Q[k] = st(Pi + S);
                 else
-                    w->Q[k] = Qp - pr->alpha * gp / (sqrt(w->gstate[k]) + pr->eps);
+                    w->Q[k] = st(Qp - pr->alpha * gp / (sqrt(w->gstate[k]) + pr->eps));
                 break;
             }
             default:
@@ -375,24 +404,24 @@ static int decode_shot(const graph *g, const uint8_t *syn, const double *prior, 
         /* Vertical update. */
         for (int e = 0; e < E; ++e) {
             int j = g->edge_var[e], h = g->edge_p[e], i = g->edge_chk[e];
-            double q[3];
+            real q[3];
             if (variant == OR_PLAIN || variant == OR_EWAINIT) {
                 /* eq. (v_update): prior plus the anticommuting messages of the other checks */
-                const double *base = (variant == OR_EWAINIT) ? &w->Pit[3 * j] : &w->Pi0[3 * j];
+                const real *base = (variant == OR_EWAINIT) ? &w->Pit[3 * j] : &w->Pi0[3 * j];
                 for (int k = 0; k < 3; ++k) {
-                    double s = 0.0;
+                    real s = 0.0;
                     for (int a = g->var_ptr[j]; a < g->var_ptr[j + 1]; ++a) {
                         int f = g->var_edges[a];
-                        if (g->edge_chk[f] != i && anticommutes(k + 1, g->edge_p[f])) s += w->m_c2v[f];
+                        if (g->edge_chk[f] != i && anticommutes(k + 1, g->edge_p[f])) s = st(s + w->m_c2v[f]);
                     }
-                    q[k] = base[k] + s;
+                    q[k] = st(base[k] + s);
                 }
             } else {
                 /* eq. (mombp5): posterior minus the raw message of this check */
                 for (int k = 0; k < 3; ++k)
-                    q[k] = w->Q[3 * j + k] - (anticommutes(k + 1, h) ? w->m_c2v[e] : 0.0);
+                    q[k] = st(w->Q[3 * j + k] - (anticommutes(k + 1, h) ? w->m_c2v[e] : 0.0));
             }
-            w->m_v2c[e] = clip(lambda_fn(h, q), c);
+            w->m_v2c[e] = st(clip(lambda_fn(h, q), c));
         }
 
     decide:
@@ -402,14 +431,14 @@ static int decode_shot(const graph *g, const uint8_t *syn, const double *prior, 
 
         if (tr) {
             size_t o3 = (size_t)(t - 1) * 3 * N;
-            if (tr->m_v2c) memcpy(tr->m_v2c + (size_t)t * E, w->m_v2c, sizeof(double) * E);
-            if (tr->m_c2v) memcpy(tr->m_c2v + (size_t)(t - 1) * E, w->m_c2v, sizeof(double) * E);
-            if (tr->S) memcpy(tr->S + o3, w->S, sizeof(double) * 3 * N);
-            if (tr->Q) memcpy(tr->Q + o3, w->Q, sizeof(double) * 3 * N);
+            if (tr->m_v2c) put(tr->m_v2c + (size_t)t * E, w->m_v2c, E);
+            if (tr->m_c2v) put(tr->m_c2v + (size_t)(t - 1) * E, w->m_c2v, E);
+            if (tr->S) put(tr->S + o3, w->S, 3 * N);
+            if (tr->Q) put(tr->Q + o3, w->Q, 3 * N);
             if (tr->aux) {
-                const double *src = (variant == OR_EWAINIT) ? w->Pit
-                                  : (variant == OR_PLAIN) ? w->Pi0 : w->gstate;
-                memcpy(tr->aux + o3, src, sizeof(double) * 3 * N);
+                const real *src = (variant == OR_EWAINIT) ? w->Pit
+                                : (variant == OR_PLAIN) ? w->Pi0 : w->gstate;
+                put(tr->aux + o3, src, 3 * N);
             }
             if (tr->dec) memcpy(tr->dec + (size_t)(t - 1) * N, w->est, N);
         }
@@ -538,4 +567,7 @@ int oracle_num_edges(int N, int M, const uint8_t *H) {
 
 /* The hard decision of Sec. II-B1 on one posterior triple (exported so that
  * the rule can be tested over every sign and tie pattern). */
-int oracle_hard_decision(const double *q) { return hard_decision(q); }
+int oracle_hard_decision(const double *q) {
+    const real r[3] = {q[0], q[1], q[2]};
+    return hard_decision(r);
+}
