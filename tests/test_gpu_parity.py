@@ -108,9 +108,37 @@ def test_messages_toric_d15(bpq, variant):
     rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5).items()}
     checked_trace(rec, H, s, prior, variant, 5, range(24), min_checked_frac=0.0)
     if variant == "adagrad":
+        # eq. (boost) applies from t = 2: iteration 1 (and the c->v messages
+        # it feeds at t = 2) is plain BP and meets the strict bar on every shot
+        for b in range(24):
+            ref = oracle.trace(H, s[b], f32(prior), variant=variant, T=5)
+            assert np.abs(rec["m_v2c"][b, :2] - ref["m_v2c"][:2]).max() <= MSG_TOL, b
+            assert np.abs(rec["m_c2v"][b, :2] - ref["m_c2v"][:2]).max() <= MSG_TOL, b
         # with eps = 1 the boosted step is well-conditioned: strict bar on every shot
         rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant=variant, T=5, eps=1.0).items()}
         assert compare_trace(rec, H, s, prior, variant, 5, range(24), eps=1.0) == 24
+
+
+def test_messages_toric_d15_adagrad_low_p(bpq):
+    """AdaGrad-BP at the paper's alpha = 5 and eps = 1e-8 on toric d = 15 at
+    p = 0.02, 48 shots, five iterations.  Where a (qubit, Pauli) pair's
+    anticommuting messages cancel, G is ~0 at the first boosted step and the
+    oracle itself moves by O(1) under an 8-ulp prior perturbation (on every
+    shot from p = 0.06 up).  At p = 0.02 about 29 % of shots have no such
+    pair: every shot whose oracle sensitivity stays below 1e-5 must meet the
+    strict 1e-4 bar, and at least a quarter of the shots must be such; the
+    others are held to the conditioned bar."""
+    t = bpq.Tanner("toric", 15)
+    H = t.dense()
+    ch = oracle.depolarizing(0.02)
+    _, s = oracle.sample(H, *ch, seed=0xB9E00001, shot0=1000, B=48)
+    prior = np.tile(ch, (t.N, 1))
+    syn, pri = gpu_inputs(bpq, t, s, prior)
+    rec = {k: v.cpu().numpy() for k, v in bpq.decode_trace(t, syn, pri, variant="adagrad", T=5).items()}
+    stable = [b for b in range(48) if oracle_sensitivity(H, s, prior, "adagrad", 5, b) < 1e-5]
+    assert len(stable) >= 12, len(stable)
+    assert compare_trace(rec, H, s, prior, "adagrad", 5, stable) == len(stable)
+    compare_trace(rec, H, s, prior, "adagrad", 5, [b for b in range(48) if b not in stable], conditioned=True)
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -210,17 +238,73 @@ def test_decode_planar_d5_10k_shots(bpq, variant):
     assert (fail_g[conv == 1] != 1).all() and (fail_g[conv == 0] == 1).all()
 
 
+# EWAInit-BP's state forgets its past as (1 - alpha)^t (eq. (EWAInit)); at
+# alpha = 0.5 that transient falls below binary32 resolution after 24
+# iterations.  A shot that the FP64 oracle converges by then has the same
+# outcome at every working precision (tests/test_oracle_precision.py); later
+# convergence at uniform priors is decided by the precision (Sec. IV-A).
+ROBUST_ITERS = 24
+
+
+def row_hashes(est):
+    import hashlib
+    est = np.ascontiguousarray(est, dtype=np.uint8)
+    return np.array([int.from_bytes(hashlib.blake2b(r.tobytes(), digest_size=4).digest(), "little") for r in est],
+                    dtype=np.uint32)
+
+
+@pytest.mark.parametrize("p,seed", [(0.02, 0xB9E00001), (0.04, 0xB9E00002)])
+@pytest.mark.parametrize("kind,d", [("toric", 15), ("toric", 10), ("planar", 15)])
+def test_low_p_ewainit_uniform_priors(bpq, kind, d, p, seed):
+    """EWAInit-BP at the paper's uniform priors (depolarising p/3 per Pauli),
+    4000 shots, at most 100 iterations, against the FP64 oracle's stored
+    outcomes (tests/golden/lowp_ewainit_oracle.npz).  With uniform priors
+    many trapping sets sit in a nearly symmetric oscillation that EWAInit-BP
+    leaves only through asymmetries below binary32 resolution, so on shots
+    that converge late (or never) the fp32 kernel and the FP64 oracle may
+    legitimately differ; the FP64 oracle and its own long-double build
+    already do on more than 0.1 % of shots.  On the precision-robust shots
+    (the oracle converges within ROBUST_ITERS iterations) the bars are the
+    strict ones: convergence, logical outcome and estimate equal on at least
+    99.9 % of shots."""
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "lowp_ewainit_oracle.npz"))
+    key = f"{kind}{d}_p{p:.2f}"
+    B = 4000
+    conv_r = np.unpackbits(g[key + "_conv"])[:B].astype(bool)
+    fail_r = np.unpackbits(g[key + "_fail"])[:B].astype(bool)
+    iters_r = g[key + "_iters"]
+    t = bpq.Tanner(kind, d)
+    ch = oracle.depolarizing(p)
+    err_g, syn_g = bpq.sample(t, *ch, seed=seed, shot0=0, B=B)
+    est, conv, iters = bpq.decode(t, syn_g, bpq.prior_tensor(t, *ch), "ewainit", max_iter=100, alpha=0.5)
+    fail_g = bpq.check_logical(t, err_g, est)
+    torch.cuda.synchronize()
+    est, conv, iters, fail_g = (x.cpu().numpy() for x in (est, conv, iters, fail_g))
+    conv = conv.astype(bool)
+    assert (fail_g[conv] != 1).all() and (fail_g[~conv] == 1).all()
+    R = conv_r & (iters_r <= ROBUST_ITERS)
+    assert R.mean() >= 0.85, R.mean()
+    assert conv[R].mean() >= 0.999, conv[R].mean()
+    assert ((fail_g[R] > 0) == fail_r[R]).mean() >= 0.999
+    assert (row_hashes(est[R]) == g[key + "_est"][R]).mean() >= 0.999
+    # the late and unconverged shots: a binary32 decoder resolves fewer
+    # near-symmetric states than FP64, never more on average
+    print(f"{key}: robust {R.mean():.4f}; unconverged GPU {1 - conv.mean():.4f}, oracle {1 - conv_r.mean():.4f}; "
+          f"LER GPU {(fail_g > 0).mean():.5f}, oracle {fail_r.mean():.5f}")
+    assert (1 - conv.mean()) >= (1 - conv_r.mean()) - 2 * np.sqrt(max(1 - conv_r.mean(), 1.0 / B) / B)
+
+
 @pytest.mark.parametrize("kind,d", [("toric", 10), ("toric", 15), ("planar", 15)])
 def test_low_p_ewainit_on_jittered_priors(bpq, kind, d):
     """EWAInit-BP at depolarising p = 0.02, 4000 shots, at most 100
-    iterations, on priors jittered by 2^-16 per qubit (prior_rows).  With
-    exactly uniform priors some syndromes leave the decoder in an exactly
-    symmetric state that EWAInit-BP cannot break under the parallel schedule
-    (Sec. V-A), and whether a run escapes then depends only on rounding.  The
-    jitter breaks those ties in the input, so both sides must agree on
-    convergence and on the logical outcome.  Converged estimates that differ
-    must be degenerate equivalents; shots that run to max_iter have no
-    unique answer and are only checked for validity."""
+    iterations, on priors jittered by 2^-16 per qubit (prior_rows).  The
+    jitter puts the asymmetry that breaks the trapping sets' oscillation into
+    the input, where binary32 resolves it, so both sides must agree on
+    convergence and on the logical outcome of at least 99.9 % of shots, and on
+    the estimate of at least 99.9 % of the precision-robust ones.  Converged
+    estimates that differ elsewhere must be degenerate equivalents (equal
+    logical outcome); shots that run to max_iter have no unique answer and
+    are only checked for validity."""
     from inputs import jittered_priors
     t = bpq.Tanner(kind, d)
     H = t.dense()
@@ -236,14 +320,14 @@ def test_low_p_ewainit_on_jittered_priors(bpq, kind, d):
     est, conv, iters, fail_g = (x.cpu().numpy() for x in (est, conv, iters, fail_g))
 
     e_ref, s_ref = oracle.sample(H, *ch, seed=0xB9E00001, shot0=0, B=B)
-    est_r, conv_r, _ = oracle.decode(H, s_ref, rows.astype(np.float64), "ewainit", max_iter=100, alpha=0.5,
-                                     nthreads=NTHREADS)
+    est_r, conv_r, iters_r = oracle.decode(H, s_ref, rows.astype(np.float64), "ewainit", max_iter=100, alpha=0.5,
+                                           nthreads=NTHREADS)
     fail_r, _ = codes.logical_failure(H, e_ref, est_r)
     conv = conv.astype(bool)
-    assert (conv == conv_r).mean() >= 0.998, (conv == conv_r).mean()
-    assert ((fail_g > 0) == fail_r).mean() >= 0.998
-    both = conv & conv_r
-    assert (est[both] == est_r[both]).all(axis=1).mean() >= 0.998
+    assert (conv == conv_r).mean() >= 0.999, (conv == conv_r).mean()
+    assert ((fail_g > 0) == fail_r).mean() >= 0.999
+    R = conv_r & (iters_r <= ROBUST_ITERS)
+    assert (est[R] == est_r[R]).all(axis=1).mean() >= 0.999
     pg, sg = ler_interval(fail_g > 0)
     pr, sr = ler_interval(fail_r)
     assert abs(pg - pr) <= max(sg, sr), (pg, pr)
@@ -385,17 +469,21 @@ def test_decode_host_pipelined_matches_device(bpq):
         assert torch.equal(a.cpu(), b)
 
 
-@pytest.mark.parametrize("p,min_stable", [(0.08, 0.75), (0.14, 0.15)])
-def test_full_size_toric_d15_bench_configuration(bpq, p, min_stable):
-    """The bench configuration: toric d = 15, 10^6 shots at one p, EWAInit-BP,
-    max 100 iterations, the default launch shape.  Invariants on every shot;
-    decisions on 200 shots spread over the batch against the oracle (on the
-    shots whose oracle decision is stable under an 8-ulp prior perturbation;
-    see test_batched_results_match_oracle_sample)."""
+@pytest.mark.parametrize("p,k", [(0.06, 2), (0.14, 6)])
+def test_full_size_toric_d15_bench_configuration(bpq, p, k):
+    """The bench configuration: toric d = 15, 10^6 shots at one p of the
+    sweep (seed 0xB9E00001 + k), EWAInit-BP, max 100 iterations, the default
+    launch shape.  Invariants on every shot.  Shots 0..999 of the launch are
+    the stored sweep shots (tests/golden/toric15_sweep_oracle.npz): on the
+    precision-robust ones (the oracle's binary32-storage build agrees with
+    FP64) convergence, logical outcome and converged estimates must agree on
+    at least 99.9 %.  100 more shots spread over the rest of the batch (those
+    decoded last by the persistent grid included) are compared with a live
+    oracle run in the same way."""
     t = bpq.Tanner("toric", 15)
     ch = oracle.depolarizing(p)
     B = 1_000_000
-    err, syn = bpq.sample(t, *ch, seed=0xB9E00001, shot0=0, B=B)
+    err, syn = bpq.sample(t, *ch, seed=0xB9E00001 + k, shot0=0, B=B)
     prior = bpq.prior_tensor(t, *ch)
     est, conv, iters = bpq.decode(t, syn, prior, "ewainit", max_iter=100)
     fail = bpq.check_logical(t, err, est)
@@ -405,21 +493,34 @@ def test_full_size_toric_d15_bench_configuration(bpq, p, min_stable):
     assert (iters_c[conv_c == 0] == 100).all()
     assert (fail_c[conv_c == 1] != 1).all() and (fail_c[conv_c == 0] == 1).all()
 
-    idx = np.linspace(0, B - 1, 200).astype(np.int64)
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "toric15_sweep_oracle.npz"))
+    key = f"ewainit_p{p:.2f}"
+    n = 1000
+    unpack = lambda a: np.unpackbits(g[key + a])[:n].astype(bool)
+    conv_r, fail_r, robust = unpack("_conv"), unpack("_fail"), unpack("_robust")
+    est_head = est[:n].cpu().numpy()
+    R = robust
+    assert R.mean() >= 0.96
+    assert ((conv_c[:n] == 1)[R] == conv_r[R]).mean() >= 0.999
+    assert ((fail_c[:n] > 0)[R] == fail_r[R]).mean() >= 0.999
+    both = R & conv_r & (conv_c[:n] == 1)
+    assert (row_hashes(est_head[both]) == g[key + "_est"][both]).mean() >= 0.999
+
+    idx = np.linspace(n, B - 1, 100).astype(np.int64)
     H = t.dense()
-    s_ref = np.concatenate([oracle.sample(H, *ch, seed=0xB9E00001, shot0=int(i), B=1)[1] for i in idx])
+    e_ref = np.concatenate([oracle.sample(H, *ch, seed=0xB9E00001 + k, shot0=int(i), B=1)[0] for i in idx])
+    s_ref = np.concatenate([oracle.sample(H, *ch, seed=0xB9E00001 + k, shot0=int(i), B=1)[1] for i in idx])
     pri = f32(np.tile(ch, (t.N, 1)))
-    est_r, conv_r, iters_r = oracle.decode(H, s_ref, pri, "ewainit", max_iter=100, nthreads=NTHREADS)
-    rng = np.random.default_rng(11)
-    stable = np.ones(len(idx), dtype=bool)
-    for _ in range(3):
-        pp = pri * (1 + 2.0 ** -20 * rng.choice([-1.0, 1.0], size=pri.shape))
-        stable &= (oracle.decode(H, s_ref, pp, "ewainit", max_iter=100, nthreads=NTHREADS)[0] == est_r).all(axis=1)
-    same = (est[torch.from_numpy(idx).cuda()].cpu().numpy() == est_r).all(axis=1)
-    # above the toric code's threshold region most shots never converge and
-    # their 100-iteration trajectories are chaotic (unstable in the oracle too)
-    assert stable.mean() >= min_stable
-    assert same[stable].mean() >= 0.999, (same[stable].mean(), stable.mean())
+    r64 = oracle.decode(H, s_ref, pri, "ewainit", max_iter=100, nthreads=NTHREADS)
+    r32 = oracle.decode(H, s_ref, pri, "ewainit", max_iter=100, nthreads=NTHREADS, precision="f32")
+    f64 = codes.logical_failure(H, e_ref, r64[0])[0]
+    f32b = codes.logical_failure(H, e_ref, r32[0])[0]
+    R = (r64[1] == r32[1]) & (f64 == f32b) & (~r64[1] | (r64[0] == r32[0]).all(axis=1))
+    assert R.mean() >= 0.9
+    sel = torch.from_numpy(idx).cuda()
+    est_s, conv_s, fail_s = est[sel].cpu().numpy(), conv[sel].cpu().numpy() == 1, fail[sel].cpu().numpy() > 0
+    assert (conv_s[R] == r64[1][R]).all() and (fail_s[R] == f64[R]).all()
+    assert (est_s[R & r64[1]] == r64[0][R & r64[1]]).all()
 
 
 @pytest.mark.parametrize("L", [3, 7, 11])

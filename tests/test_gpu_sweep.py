@@ -1,0 +1,102 @@
+"""Decoding-outcome parity with the FP64 oracle across the bench's toric
+d = 15 sweep (Sec. IV-B2: toric code, parallel schedule, at most 100
+iterations), for plain BP, Momentum-BP, AdaGrad-BP and EWAInit-BP at the
+paper's parameters, 1000 shots at each of p = 0.02, 0.06, 0.10, 0.14.
+
+The oracle's outcomes come from tests/golden/toric15_sweep_oracle.npz,
+written by tests/golden/make_oracle_outcomes.py (which calls only oracle/);
+an FP64 oracle run of this size would take many minutes on the test host,
+whose long double is software binary128.  test_oracle_outcomes_file.py
+re-derives a sample of the file on the CPU.
+
+A shot is precision-robust when the oracle's binary32-storage build gives
+the same convergence flag, logical outcome and (if converged) estimate as
+the FP64 build; its answer is then the method's, not the rounding's.  On
+those shots the GPU must agree on at least 99.9 % of convergence flags and
+logical outcomes and on at least 99.9 % of the converged estimates, and the
+logical error rates on them must lie inside each other's 2-sigma binomial
+interval.  The fraction of shots that are not precision-robust is bounded by
+what the oracle itself measures (plain BP and Momentum-BP: none), and every
+GPU output must be valid (a converged shot satisfies its syndrome, an
+unconverged one ran max_iter iterations)."""
+import hashlib
+import os
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "toric15_sweep_oracle.npz")
+P_SWEEP = (0.02, 0.06, 0.10, 0.14)
+K_OF_P = {0.02: 0, 0.06: 2, 0.10: 4, 0.14: 6}
+SHOTS = 1000
+# the largest fraction of shots whose oracle outcome the precision decides,
+# per variant, as the two oracle builds measure it on this workload
+# (EWAInit-BP: 1.6-2.5 % by convergence and outcome, more by the estimates of
+# unconverged shots, which run 100 chaotic iterations and are not compared;
+# AdaGrad-BP: 4.3 % at p = 0.06, where its boosted step is ill-conditioned)
+MAX_UNROBUST = {"plain": 0.0, "momentum": 0.0, "adagrad": 0.06, "ewainit": 0.04}
+
+
+def row_hashes(est: np.ndarray) -> np.ndarray:
+    est = np.ascontiguousarray(est, dtype=np.uint8)
+    return np.array([int.from_bytes(hashlib.blake2b(r.tobytes(), digest_size=4).digest(), "little") for r in est],
+                    dtype=np.uint32)
+
+
+@pytest.fixture(scope="module")
+def golden():
+    return np.load(GOLDEN)
+
+
+@pytest.fixture(scope="module")
+def bpq():
+    import paper_2407_11523_gb300 as bpq
+    assert torch.cuda.is_available()
+    return bpq
+
+
+def ler_interval(fails):
+    n = max(fails.size, 1)
+    p = fails.mean() if fails.size else 0.0
+    return p, 2 * np.sqrt(max(p * (1 - p), 1.0 / n) / n)
+
+
+@pytest.mark.parametrize("p", P_SWEEP)
+@pytest.mark.parametrize("variant", ["plain", "momentum", "adagrad", "ewainit"])
+def test_sweep_outcomes_match_oracle(bpq, golden, variant, p):
+    key = f"{variant}_p{p:.2f}"
+    unpack = lambda a: np.unpackbits(golden[key + a])[:SHOTS].astype(bool)
+    conv_r, fail_r, robust = unpack("_conv"), unpack("_fail"), unpack("_robust")
+    est_h = golden[key + "_est"]
+
+    t = bpq.Tanner("toric", 15)
+    ch = (p / 3, p / 3, p / 3)
+    err, syn = bpq.sample(t, *ch, seed=0xB9E00001 + K_OF_P[p], shot0=0, B=SHOTS)
+    est, conv, iters = bpq.decode(t, syn, bpq.prior_tensor(t, *ch), variant, max_iter=100)
+    fail = bpq.check_logical(t, err, est)
+    torch.cuda.synchronize()
+    est, conv, iters, fail = (x.cpu().numpy() for x in (est, conv, iters, fail))
+    conv = conv.astype(bool)
+
+    # every output is valid
+    assert (fail[conv] != 1).all() and (fail[~conv] == 1).all()
+    assert ((iters >= 1) & (iters <= 100)).all() and (iters[~conv] == 100).all()
+
+    assert 1.0 - robust.mean() <= MAX_UNROBUST[variant] + 1e-9, (key, robust.mean())
+    R = robust
+    assert (conv[R] == conv_r[R]).mean() >= 0.999, (key, (conv[R] == conv_r[R]).mean())
+    assert ((fail[R] > 0) == fail_r[R]).mean() >= 0.999, key
+    both = R & conv & conv_r
+    if both.any():
+        same = row_hashes(est[both]) == est_h[both]
+        assert same.mean() >= 0.999, (key, same.mean())
+    pg, sg = ler_interval(fail[R] > 0)
+    pr, sr = ler_interval(fail_r[R])
+    assert abs(pg - pr) <= max(sg, sr), (key, pg, pr)
+    print(f"{key}: robust {R.mean():.3f}, GPU LER {(fail > 0).mean():.4f} (on robust {pg:.4f}), "
+          f"oracle LER {fail_r.mean():.4f} (on robust {pr:.4f}), converged GPU {conv.mean():.3f} oracle "
+          f"{conv_r.mean():.3f}")
