@@ -349,7 +349,7 @@ def run_ours(args, rank, world):
 
     # untimed EWAInit-BP pass on priors jittered by 2^-16 per qubit: uniform
     # priors leave exactly symmetric states that the parallel schedule cannot
-    # break (Sec. V-A), so part of the uniform-prior failures at low p are
+    # break (Sec. IV-A), so part of the uniform-prior failures at low p are
     # rounding-decided ties; the jitter breaks them in the input
     if "ewainit" in results and not args.no_jitter_ler:
         rel = 2.0 ** -16

@@ -198,10 +198,16 @@ int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *
  * (about 16000 toric d = 15 shots); larger batches return BPQ_EINVAL with a
  * message.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the one array, which keeps the last
- * call's contents (the shot queue is reset on every call): calls that may
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Arguments and errors otherwise as
+ * stream capture.  The cached address does not survive a cudaDeviceReset:
+ * resetting a device after that first call is not supported.  With CUDA's
+ * default lazy module loading, the first launch of each decode kernel (one
+ * per variant and message layout, see bpq_tanner_layout) loads its module,
+ * and the driver may allocate device memory for it: make one warm-up call
+ * per variant and code family before the loop that must not allocate, or
+ * run with CUDA_MODULE_LOADING=EAGER.  All calls share the one array, which
+ * keeps the last call's contents (the shot queue is reset on every call):
+ * calls that may overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.  Arguments and errors otherwise as
  * bpq_decode_host; the stream is synchronized before returning. */
 int bpq_decode_host_noalloc(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
                             const bpq_params *params, int max_iter, int B, uint8_t *est_host, uint8_t *conv_host,

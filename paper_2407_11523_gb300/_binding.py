@@ -257,12 +257,14 @@ def prior_rows(n_qubits: int, px, py, pz, jitter: float = 0.0) -> np.ndarray:
     u_j = 2 * ((j * 2654435761) mod 2^32) / 2^32 - 1 lies in [-1, 1).  The
     result is computed in float64 and rounded once to float32.
 
-    Uniform priors on the toric and planar codes leave syndromes whose BP
-    state is exactly symmetric (the trapping sets of Sec. II-B2).  Under the
-    parallel schedule EWAInit-BP cannot break such a symmetry by itself
-    (Sec. V-A), so whether a run escapes depends only on the rounding
-    asymmetries of the arithmetic.  A jitter of 2^-16 makes the escape
-    deterministic, and it is far below any channel-estimation precision."""
+    Uniform priors on the toric and planar codes put many trapping sets
+    (Sec. II-B2) into a nearly symmetric oscillation.  Under the parallel
+    schedule EWAInit-BP cannot break an exact symmetry by itself (Sec.
+    IV-A); a near one breaks only through asymmetries far below binary32
+    resolution, so whether a run escapes is decided by the working
+    precision.  A jitter of 2^-16 puts the asymmetry into the input, where
+    every precision resolves it, and it is far below any channel-estimation
+    precision."""
     j = np.arange(n_qubits, dtype=np.uint64)
     u = ((j * np.uint64(2654435761)) % np.uint64(1 << 32)).astype(np.float64) / 2.0 ** 32 * 2.0 - 1.0
     ch = np.array([px, py, pz], dtype=np.float64)

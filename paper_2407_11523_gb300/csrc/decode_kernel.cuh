@@ -66,6 +66,13 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (TMA) accesses; with a CTA barrier after it, a bulk copy
+// issued by one thread cannot be overtaken by other threads' earlier stores.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
@@ -784,10 +791,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
         if (g < 0) break;
         from = g;
         if (g != cur) {
-            // switch code: descriptor, adjacency (bulk TMA), prior, zero slots
+            // switch code: descriptor, adjacency (bulk TMA), prior, zero slots.
+            // The new table may cover the previous item's prior, message slots
+            // and state, written with ordinary stores: every thread fences
+            // them against the async proxy before the barrier that precedes
+            // the copy.
             const uint32_t *src = reinterpret_cast<const uint32_t *>(b.codes + g);
             for (int w = tid; w < (int)(sizeof(DecodeArgs) / 4); w += blockDim.x)
                 reinterpret_cast<uint32_t *>(desc)[w] = src[w];
+            fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
                 mbar_expect_tx(mbar, desc->table_bytes);

@@ -50,7 +50,7 @@ def jittered_priors(n_qubits: int, px: float, py: float, pz: float, rel: float):
     is done in float64 and rounded once to float32, so the rows are exact
     and identical wherever they are built.  rel = 0 gives the uniform rows.
     A tiny rel breaks the exact symmetric ties that uniform priors leave on
-    the toric and planar codes (Sec. II-B2, Sec. V-A)."""
+    the toric and planar codes (Sec. II-B2, Sec. IV-A)."""
     j = np.arange(n_qubits, dtype=np.uint64)
     u = ((j * np.uint64(2654435761)) % np.uint64(1 << 32)).astype(np.float64) / 2.0 ** 32 * 2.0 - 1.0
     ch = np.array([px, py, pz], dtype=np.float64)

@@ -119,7 +119,7 @@ def test_trapping_set_parallel_never_converges(per_pauli):
 
 def test_prior_jitter_breaks_the_exact_symmetry():
     """Under the parallel schedule EWAInit-BP cannot leave the symmetric
-    (4,0) trapping set by itself (Sec. V-A); any asymmetry in the input priors
+    (4,0) trapping set by itself (Sec. IV-A); any asymmetry in the input priors
     is amplified by the prior re-initialisation of eq. (EWAInit) until the
     decisions split and satisfy the syndrome.  Plain BP has no such
     amplification and keeps oscillating."""

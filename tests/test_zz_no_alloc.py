@@ -21,6 +21,9 @@ def _p(t):
 
 
 def test_noalloc_matches_decode_host_on_two_calls():
+    """Two calls in a row on different batches give bpq_decode_host's
+    results, and the second call (the kernel's module already loaded by the
+    first) leaves the device's free memory unchanged."""
     import paper_2407_11523_gb300 as bpq
 
     L = bpq.lib()
@@ -29,19 +32,27 @@ def test_noalloc_matches_decode_host_on_two_calls():
     assert max_shots >= 8192
     stream = torch.cuda.current_stream()
     params = bpq.make_params("ewainit", alpha=0.5)
-    for call, (p, B, seed) in enumerate([(0.08, 4000, 11), (0.12, 2500, 12)]):
+    calls = []
+    for p, B, seed in [(0.08, 4000, 11), (0.12, 2500, 12)]:
         _, syn = bpq.sample(t, p / 3, p / 3, p / 3, seed=seed, shot0=0, B=B)
         syn_h = syn.cpu().pin_memory()
         prior_h = bpq.prior_tensor(t, p / 3, p / 3, p / 3).cpu().pin_memory()
         ref = bpq.decode_host(t, syn_h, prior_h, "ewainit", params=params, max_iter=100)
-        est = torch.zeros((B, t.N), dtype=torch.uint8, pin_memory=True)
-        conv = torch.zeros(B, dtype=torch.uint8, pin_memory=True)
-        iters = torch.zeros(B, dtype=torch.uint8, pin_memory=True)
+        outs = (torch.zeros((B, t.N), dtype=torch.uint8, pin_memory=True),
+                torch.zeros(B, dtype=torch.uint8, pin_memory=True),
+                torch.zeros(B, dtype=torch.uint8, pin_memory=True))
+        calls.append((B, syn_h, prior_h, ref, outs))
+    torch.cuda.synchronize()
+    free = []
+    for B, syn_h, prior_h, ref, (est, conv, iters) in calls:
         rc = L.bpq_decode_host_noalloc(t.handle, _p(syn_h), _p(prior_h), bpq.EWAINIT, ctypes.byref(params), 100, B,
                                        _p(est), _p(conv), _p(iters), ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, L.bpq_last_error()
+        free.append(torch.cuda.mem_get_info()[0])
+    assert free[1] == free[0], free
+    for k, (B, syn_h, prior_h, ref, (est, conv, iters)) in enumerate(calls):
         # integer outputs of the same kernel on the same inputs: identical
-        assert torch.equal(est, ref[0]) and torch.equal(conv, ref[1]) and torch.equal(iters, ref[2]), call
+        assert torch.equal(est, ref[0]) and torch.equal(conv, ref[1]) and torch.equal(iters, ref[2]), k
         assert int(conv.sum()) > 0
 
 
