@@ -19,9 +19,12 @@ Files (numpy .npz, one group of arrays per workload <key>):
 Per workload: <key>_conv and <key>_fail (bit-packed bools: converged, and
 the residual is not a stabilizer, Sec. IV), <key>_iters (uint8),
 <key>_est (uint32: the first four bytes of blake2b(estimate row), so that
-estimates can be compared without storing them), <key>_robust (bit-packed:
-the binary32-storage build of the oracle gives the same convergence flag,
-logical outcome and, for converged shots, estimate; sweep file only).
+estimates can be compared without storing them), <key>_robust (bit-packed,
+sweep file only): the shot's outcome does not depend on the rounding, i.e.
+the binary32-storage build of the oracle and three FP64 runs on priors
+perturbed by 8 binary32 ulps (each probability scaled by 1 +- 2^-20, random
+signs) all give the same convergence flag, logical outcome and, for
+converged shots, estimate as the FP64 run.
 """
 from __future__ import annotations
 
@@ -61,6 +64,23 @@ def lowp_key(kind: str, d: int, p: float) -> str:
     return f"{kind}{d}_p{p:.2f}"
 
 
+PERTURBATIONS = 3
+
+
+def perturbed(prior: np.ndarray, n_qubits: int, seed: int, r: int) -> np.ndarray:
+    """(N, 3) priors with every probability scaled by 1 +- 2^-20 (8 ulps of
+    binary32), signs from numpy's seeded generator."""
+    rows = np.tile(np.asarray(prior, dtype=np.float64).reshape(1, 3), (n_qubits, 1))
+    rng = np.random.default_rng([seed, r])
+    return rows * (1 + 2.0 ** -20 * rng.choice([-1.0, 1.0], size=rows.shape))
+
+
+def same_outcome(a, b):
+    est_a, conv_a, _, fail_a = a
+    est_b, conv_b, _, fail_b = b
+    return (conv_a == conv_b) & (fail_a == fail_b) & (~conv_a | (est_a == est_b).all(axis=1))
+
+
 def outcomes(H, err, syn, prior, variant, precision, nthreads):
     est, conv, iters = oracle.decode(H, syn, prior, variant, max_iter=MAX_ITER, nthreads=nthreads,
                                      precision=precision)
@@ -76,10 +96,13 @@ def main() -> None:
         ch = oracle.depolarizing(p)
         err, syn = oracle.sample(H, *ch, seed=0xB9E00001 + SWEEP_K[p], shot0=0, B=SWEEP_SHOTS)
         prior = np.asarray(ch, dtype=np.float32).astype(np.float64)
-        for v in SWEEP_VARIANTS:
-            est, conv, iters, fail = outcomes(H, err, syn, prior, v, "f64", nthreads)
-            est32, conv32, _, fail32 = outcomes(H, err, syn, prior, v, "f32", nthreads)
-            robust = (conv32 == conv) & (fail32 == fail) & (~conv | (est32 == est).all(axis=1))
+        for vi, v in enumerate(SWEEP_VARIANTS):
+            ref = outcomes(H, err, syn, prior, v, "f64", nthreads)
+            est, conv, iters, fail = ref
+            robust = same_outcome(ref, outcomes(H, err, syn, prior, v, "f32", nthreads))
+            for r in range(PERTURBATIONS):
+                pp = perturbed(prior, H.shape[1], seed=1000 * vi + SWEEP_K[p], r=r)
+                robust &= same_outcome(ref, outcomes(H, err, syn, pp, v, "f64", nthreads))
             k = sweep_key(v, p)
             out[k + "_conv"] = np.packbits(conv)
             out[k + "_fail"] = np.packbits(fail)

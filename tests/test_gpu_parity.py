@@ -475,9 +475,9 @@ def test_full_size_toric_d15_bench_configuration(bpq, p, k):
     sweep (seed 0xB9E00001 + k), EWAInit-BP, max 100 iterations, the default
     launch shape.  Invariants on every shot.  Shots 0..999 of the launch are
     the stored sweep shots (tests/golden/toric15_sweep_oracle.npz): on the
-    precision-robust ones (the oracle's binary32-storage build agrees with
-    FP64) convergence, logical outcome and converged estimates must agree on
-    at least 99.9 %.  100 more shots spread over the rest of the batch (those
+    precision-robust ones (the oracle's binary32-storage build and 8-ulp
+    prior perturbations agree with FP64) convergence, logical outcome and
+    converged estimates must agree on at least 99.9 %.  100 more shots spread over the rest of the batch (those
     decoded last by the persistent grid included) are compared with a live
     oracle run in the same way."""
     t = bpq.Tanner("toric", 15)
@@ -500,7 +500,7 @@ def test_full_size_toric_d15_bench_configuration(bpq, p, k):
     conv_r, fail_r, robust = unpack("_conv"), unpack("_fail"), unpack("_robust")
     est_head = est[:n].cpu().numpy()
     R = robust
-    assert R.mean() >= 0.96
+    assert R.mean() >= 0.88
     assert ((conv_c[:n] == 1)[R] == conv_r[R]).mean() >= 0.999
     assert ((fail_c[:n] > 0)[R] == fail_r[R]).mean() >= 0.999
     both = R & conv_r & (conv_c[:n] == 1)
@@ -512,11 +512,17 @@ def test_full_size_toric_d15_bench_configuration(bpq, p, k):
     s_ref = np.concatenate([oracle.sample(H, *ch, seed=0xB9E00001 + k, shot0=int(i), B=1)[1] for i in idx])
     pri = f32(np.tile(ch, (t.N, 1)))
     r64 = oracle.decode(H, s_ref, pri, "ewainit", max_iter=100, nthreads=NTHREADS)
-    r32 = oracle.decode(H, s_ref, pri, "ewainit", max_iter=100, nthreads=NTHREADS, precision="f32")
     f64 = codes.logical_failure(H, e_ref, r64[0])[0]
-    f32b = codes.logical_failure(H, e_ref, r32[0])[0]
-    R = (r64[1] == r32[1]) & (f64 == f32b) & (~r64[1] | (r64[0] == r32[0]).all(axis=1))
-    assert R.mean() >= 0.9
+    # the same witnesses as the stored outcomes: binary32 storage and three
+    # 8-ulp prior perturbations must not change the FP64 outcome
+    rng = np.random.default_rng(17 + k)
+    R = np.ones(len(idx), dtype=bool)
+    for pr, prec in [(pri, "f32")] + [(pri * (1 + 2.0 ** -20 * rng.choice([-1.0, 1.0], size=pri.shape)), "f64")
+                                      for _ in range(3)]:
+        rw = oracle.decode(H, s_ref, pr, "ewainit", max_iter=100, nthreads=NTHREADS, precision=prec)
+        fw = codes.logical_failure(H, e_ref, rw[0])[0]
+        R &= (rw[1] == r64[1]) & (fw == f64) & (~r64[1] | (rw[0] == r64[0]).all(axis=1))
+    assert R.mean() >= 0.8
     sel = torch.from_numpy(idx).cuda()
     est_s, conv_s, fail_s = est[sel].cpu().numpy(), conv[sel].cpu().numpy() == 1, fail[sel].cpu().numpy() > 0
     assert (conv_s[R] == r64[1][R]).all() and (fail_s[R] == f64[R]).all()

@@ -9,14 +9,15 @@ an FP64 oracle run of this size would take many minutes on the test host,
 whose long double is software binary128.  test_oracle_outcomes_file.py
 re-derives a sample of the file on the CPU.
 
-A shot is precision-robust when the oracle's binary32-storage build gives
-the same convergence flag, logical outcome and (if converged) estimate as
-the FP64 build; its answer is then the method's, not the rounding's.  On
+A shot is precision-robust when the oracle's binary32-storage build and
+three FP64 runs on priors perturbed by 8 binary32 ulps all give the same
+convergence flag, logical outcome and (if converged) estimate as the FP64
+run; its answer is then the method's, not the rounding's.  On
 those shots the GPU must agree on at least 99.9 % of convergence flags and
 logical outcomes and on at least 99.9 % of the converged estimates, and the
 logical error rates on them must lie inside each other's 2-sigma binomial
 interval.  The fraction of shots that are not precision-robust is bounded by
-what the oracle itself measures (plain BP and Momentum-BP: none), and every
+what the oracle itself measures (plain BP: none), and every
 GPU output must be valid (a converged shot satisfies its syndrome, an
 unconverged one ran max_iter iterations)."""
 import hashlib
@@ -33,12 +34,13 @@ GOLDEN = os.path.join(HERE, "golden", "toric15_sweep_oracle.npz")
 P_SWEEP = (0.02, 0.06, 0.10, 0.14)
 K_OF_P = {0.02: 0, 0.06: 2, 0.10: 4, 0.14: 6}
 SHOTS = 1000
-# the largest fraction of shots whose oracle outcome the precision decides,
-# per variant, as the two oracle builds measure it on this workload
-# (EWAInit-BP: 1.6-2.5 % by convergence and outcome, more by the estimates of
-# unconverged shots, which run 100 chaotic iterations and are not compared;
-# AdaGrad-BP: 4.3 % at p = 0.06, where its boosted step is ill-conditioned)
-MAX_UNROBUST = {"plain": 0.0, "momentum": 0.0, "adagrad": 0.06, "ewainit": 0.04}
+# the largest fraction of shots whose oracle outcome the rounding decides,
+# per variant, as the oracle itself measures it on this workload (binary32
+# storage and three 8-ulp prior perturbations against FP64): plain BP none,
+# Momentum-BP 1.9 % (p = 0.02), AdaGrad-BP 17.5 % (p = 0.06, where its boosted
+# step is ill-conditioned), EWAInit-BP 9.9 % (p = 0.14; the near-symmetric
+# trapping-set oscillations of Sec. IV-A)
+MAX_UNROBUST = {"plain": 0.0, "momentum": 0.02, "adagrad": 0.18, "ewainit": 0.10}
 
 
 def row_hashes(est: np.ndarray) -> np.ndarray:
