@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--loads", default="1e4,1e5,1e6,1e7", help="offered loads (requests/s) for --workload serve")
     ap.add_argument("--train-model", default="ewainit", choices=["ewainit", "momentum"],
                     help="unrolled model for --workload train")
+    ap.add_argument("--shots-per-thread", type=int, default=0, choices=[0, 1, 2],
+                    help="decode kernel: 1 or 2 shots per thread (0: the library's choice, 2 on the toric codes)")
+    ap.add_argument("--launch", default="0,0", help="threads per shot group, shot groups per CTA (0,0: automatic)")
     ap.add_argument("--prior-jitter", type=float, default=0.0,
                     help="relative per-qubit prior perturbation of the timed toric15 sweep (0: the uniform "
                          "channel); an untimed EWAInit-BP pass on 2^-16-jittered priors is always reported")
@@ -228,11 +231,16 @@ def cpu_baseline(args, seconds):
         el = time.perf_counter() - t0
         if el >= seconds or (rounds + 1) * cores > cores * 64:
             break
+    import platform
+    ld = {"x86_64": "x87 80-bit", "AMD64": "x87 80-bit", "aarch64": "software IEEE binary128",
+          "arm64": "software IEEE binary128"}.get(platform.machine(), "the platform's long double")
     return {"value": done / el, "unit": "shots/s", "cores": cores, "kind": "oracle",
             "edge_updates_per_s": it_sum * 1800 / el,
             "sample": f"{rounds} rounds x {cores} shots x {len(P_SWEEP)} p values = {done} shots of the same "
                       f"workload (EWAInit-BP, shot indices from 0), {el:.1f} s wall, FP64 oracle with "
-                      f"{cores} threads"}
+                      f"{cores} threads on {platform.machine()}; its check update is evaluated in long double "
+                      f"({ld} here), which dominates its time where long double is software arithmetic",
+            "long_double": ld}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -271,6 +279,8 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     t = bpq.Tanner(CODE, DIST).upload()
+    t.set_shots_per_thread(args.shots_per_thread)
+    t.set_launch(*[int(x) for x in args.launch.split(",")])
     B = args.shots_per_p
     shot0 = shot_offset(rank, B)
     syns, errs, priors = [], [], []
@@ -348,9 +358,11 @@ def run_ours(args, rank, world):
     head = results.get("ewainit") or next(iter(results.values()))
 
     # untimed EWAInit-BP pass on priors jittered by 2^-16 per qubit: uniform
-    # priors leave exactly symmetric states that the parallel schedule cannot
-    # break (Sec. IV-A), so part of the uniform-prior failures at low p are
-    # rounding-decided ties; the jitter breaks them in the input
+    # priors put trapping sets into nearly symmetric oscillations that the
+    # parallel schedule leaves only through asymmetries below binary32
+    # resolution (Sec. IV-A), so part of the uniform-prior failures are
+    # decided by the working precision; the jitter puts the asymmetry into
+    # the input
     if "ewainit" in results and not args.no_jitter_ler:
         rel = 2.0 ** -16
         params = bpq.make_params("ewainit", **VARIANT_PARAMS["ewainit"])
@@ -386,22 +398,18 @@ def run_ours(args, rank, world):
         lat[f"batch_{nb}"] = {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
                               "launches": len(times)}
 
-    # roofline of the decode kernel: SFU-bound in-SM arithmetic.  DRAM traffic
-    # per shot comes from the committed ncu summary, used only while the
-    # kernel's code (comments and whitespace aside) still matches the
-    # profiled one.
-    traffic = issue_pct = None
+    # roofline of the decode kernel: in-SM arithmetic.  DRAM traffic per shot
+    # and the issue-slot share come from the ncu summary recorded beside the
+    # profile (profiles/*.json), used only while the kernel's code (comments
+    # and whitespace aside) still matches the profiled one.
+    traffic = issue_pct = prof_rec = None
     try:
-        prof = open(os.path.join(ROOT, "profiles", "decode_kernel_toric15_ewainit.md")).read()
+        prof_rec = json.load(open(os.path.join(ROOT, "profiles", "decode_kernel_toric15_ewainit.json")))
         src = open(os.path.join(ROOT, "paper_2407_11523_gb300", "csrc", "decode_kernel.cuh")).read()
-        want = [ln.split(":")[1].split()[0] for ln in prof.splitlines() if ln.startswith("kernel_code_sha256_16:")][0]
-        per_shot = float([ln for ln in prof.splitlines() if "traffic_bytes_per_shot:" in ln][0]
-                         .split("traffic_bytes_per_shot:")[1].split()[0])
-        if kernel_code_hash(src) == want:
-            traffic = per_shot * args.shots_per_p
-            issue_pct = float([ln for ln in prof.splitlines() if "issue_active_pct:" in ln][0]
-                              .split("issue_active_pct:")[1].split()[0])
-    except (OSError, IndexError, ValueError):
+        if kernel_code_hash(src) == prof_rec["kernel_code_sha256_16"]:
+            traffic = float(prof_rec["dram_bytes_per_shot"]) * args.shots_per_p
+            issue_pct = float(prof_rec["issue_active_pct"])
+    except (OSError, KeyError, ValueError):
         traffic = issue_pct = None
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     try:
@@ -410,18 +418,31 @@ def run_ours(args, rank, world):
         hbm_peak = None
     sfu_peak = float("nan") if args.no_probe else bpq.probe_peak("sfu", blocks=sms * 8, threads=256, iters=4096)
     fma_peak = float("nan") if args.no_probe else bpq.probe_peak("fma", blocks=sms * 8, threads=256, iters=4096)
-    # EWAInit-BP, delta form, degree-4 qubits: check side rcp + lg2, variable
-    # side ex2 + rcp per edge, and 4 ex2 per qubit shared by its 4 edges
-    sfu_per_edge_update = 5.0
+    # algorithmic work per edge-update (one c->v and one v->c message on one
+    # edge in one iteration) in the literal form of eqs. (h_update), (lambda):
+    # tanh + atanh on the check side (2 transcendental + 2 reciprocal) and a
+    # softplus and a two-term log-sum-exp on the variable side (2 ex2 + 2
+    # lg2): 8 SFU operations.  The kernel's delta form needs 5 (check side rcp
+    # + lg2, variable side ex2 + rcp per edge, 4 ex2 per degree-4 qubit).
+    sfu_per_edge_update, impl_sfu_per_edge_update = 8.0, 5.0
     ew = results.get("ewainit", head)
     kernel_sec = ew["launch_ms_mean"] / 1e3
-    achieved = sfu_per_edge_update * (ew["edge_updates_per_step"] / len(P_SWEEP)) / kernel_sec
+    eu_per_launch = ew["edge_updates_per_step"] / len(P_SWEEP)
+    achieved = sfu_per_edge_update * eu_per_launch / kernel_sec
+    impl_achieved = impl_sfu_per_edge_update * eu_per_launch / kernel_sec
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": sfu_peak / 1e12, "unit": "TSFUop/s",
                 "frac": achieved / sfu_peak, "traffic": traffic,
-                "kernel": "decode_kernel<EWAINIT>", "per_unit": f"{sfu_per_edge_update} SFU ops per edge-update",
+                "kernel": ("decode_pair_kernel<EWAINIT>" if t.shots_per_thread("ewainit") == 2 else "decode_kernel<EWAINIT>"), "per_unit": f"{sfu_per_edge_update:g} SFU ops per edge-update "
+                "(the literal form's tanh, atanh, softplus and log-sum-exp)",
+                "edge_updates_per_launch": eu_per_launch, "launch_ms": ew["launch_ms_mean"],
+                "impl_sfu_per_edge_update": impl_sfu_per_edge_update,
+                "impl_achieved": impl_achieved / 1e12, "impl_frac": impl_achieved / sfu_peak,
                 "ncu_issue_active_pct": issue_pct,
+                "ncu_summary": None if prof_rec is None else {k: prof_rec.get(k) for k in (
+                    "instructions_per_launch", "issue_active_pct", "dram_bytes_per_shot", "shots", "command")},
+                "ncu_summary_current": traffic is not None,
                 "note": "issue-bound: the SFU is not the binding unit; ncu_issue_active_pct is the share of "
-                        "issue slots used (profiles/decode_kernel_toric15_ewainit.md)",
+                        "issue slots used in the profiled launch",
                 "peak_source": "measured on this GPU by the MUFU.EX2 probe kernel (bpq_probe_peak)",
                 "fma_peak_tinst_per_s": fma_peak / 1e12, "sms": sms,
                 "hbm": {"algorithmic_bytes_per_shot": t.W * 4 + t.N + 2,

@@ -223,19 +223,38 @@ int bpq_decode_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *
                      int variant, const bpq_params *params, int T, int B, float *m_v2c_dev,
                      float *m_c2v_dev, float *Q_dev, uint8_t *dec_dev, void *work_dev, void *stream);
 
-/* Launch shape of bpq_decode: threads per shot (a multiple of 32, at most
- * 1024, covering max(N, M) with at most 2 nodes per thread, or at most 4 with
- * at most 512 threads) and shots per CTA (at most 15, or 32 for one-warp
- * shots).  0 = let the library choose (two nodes per thread, about 256
- * threads per CTA).  Stored in the handle. */
+/* Launch shape of bpq_decode: threads per shot group (a multiple of 32, at
+ * most 1024, covering max(N, M) with at most 2 nodes per thread, or at most 4
+ * with at most 512 threads) and shot groups per CTA (at most 15, or 32 for
+ * one-warp groups).  A shot group decodes one shot at a time, or two with two
+ * shots per thread (bpq_set_shots_per_thread; then at most 2 nodes per
+ * thread and 28 one-warp groups per CTA).  0 = let the library choose (two
+ * nodes per thread, about 256 threads per CTA).  Stored in the
+ * handle; bpq_get_launch reports the shape of the plain/Momentum/AdaGrad/
+ * EWAInit kernels. */
 int bpq_set_launch(bpq_tanner *t, int threads_per_shot, int shots_per_cta);
 int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_cta, int *ctas);
 
+/* Shots per thread of bpq_decode (an implementation choice; the paper has no
+ * GPU design): 1 = each thread works on one shot; 2 = each thread works on
+ * the same nodes of two shots, whose messages share 64-bit shared-memory
+ * slots and packed f32x2 arithmetic, and each of the two "lanes" takes the
+ * next shot from the queue as soon as its own shot stops (split table layout
+ * only, see bpq_tanner_layout; plain, Momentum, AdaGrad and EWAInit BP; not
+ * the trace, serial, batched or AEWA-BP paths); 0 = automatic (2 where it
+ * applies).  Per-shot results are the same bit for bit either way.
+ * bpq_get_shots_per_thread reports what bpq_decode will use for `variant`.
+ * Errors: EINVAL (value outside 0..2, 2 on a table without the split
+ * layout, a stored launch shape that does not fit). */
+int bpq_set_shots_per_thread(bpq_tanner *t, int shots_per_thread);
+int bpq_get_shots_per_thread(const bpq_tanner *t, int variant, int *shots_per_thread);
+
 /* Autotuner of the launch shape (an addition; the paper has no GPU design):
  * times bpq_decode on the caller's sample batch (same arguments as
- * bpq_decode) for every candidate shape - 1..4 nodes per thread, 1..32
- * shots per CTA - and stores the fastest in the
- * handle (as bpq_set_launch would).  Synchronizes `stream`; the outputs are
+ * bpq_decode) for every candidate shape - one or two shots per thread, 1..4
+ * nodes per thread (1..2 with two shots per thread), 1..32 shot groups per
+ * CTA - and stores the fastest in the handle (as bpq_set_launch and
+ * bpq_set_shots_per_thread would).  Synchronizes `stream`; the outputs are
  * those of the last trial.  Reports the chosen shape and its time per
  * launch (any output pointer may be NULL). */
 int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,

@@ -71,6 +71,8 @@ def lib():
             "bpq_autotune": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, P, pi, pi,
                                  ctypes.POINTER(ctypes.c_float)]),
             "bpq_get_launch": (i, [P, pi, pi, pi]),
+            "bpq_set_shots_per_thread": (i, [P, i]),
+            "bpq_get_shots_per_thread": (i, [P, i, pi]),
             "bpq_check_logical": (i, [P, P, P, i, P, P]),
             "bpq_probe_peak": (i, [i, i, i, i, P, P]),
             "bpq_batch_workspace_bytes": (sz, [i]),
@@ -212,6 +214,17 @@ class Tanner:
         t, s, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().bpq_get_launch(self._h, ctypes.byref(t), ctypes.byref(s), ctypes.byref(c)), "bpq_get_launch")
         return t.value, s.value
+
+    def set_shots_per_thread(self, k=0):
+        """1: one shot per thread; 2: two shots per thread (split tables);
+        0: automatic (bpq_set_shots_per_thread)."""
+        _check(lib().bpq_set_shots_per_thread(self._h, k), "bpq_set_shots_per_thread")
+
+    def shots_per_thread(self, variant="ewainit") -> int:
+        k = ctypes.c_int()
+        _check(lib().bpq_get_shots_per_thread(self._h, VARIANTS.get(variant, variant), ctypes.byref(k)),
+               "bpq_get_shots_per_thread")
+        return k.value
 
 
 def autotune(tanner: Tanner, syn, prior, variant="ewainit", params=None, max_iter=100, stream=None, **param_kw):

@@ -563,12 +563,33 @@ int bpq_set_launch(bpq_tanner *t, int threads_per_shot, int shots_per_cta) {
     t->threads_per_shot = threads_per_shot;
     t->shots_per_cta = shots_per_cta;
     bpq::LaunchShape s;
-    int rc = bpq::decode_launch_shape(t, -1, &s);
+    int rc = bpq::decode_uses_pairs(t, BPQ_MOMENTUM, false) ? bpq::decode_pair_shape(t, BPQ_MOMENTUM, &s)
+                                                            : bpq::decode_launch_shape(t, -1, &s);
     if (rc) {
         t->threads_per_shot = old_t;
         t->shots_per_cta = old_s;
     }
     return rc;
+}
+
+int bpq_set_shots_per_thread(bpq_tanner *t, int shots_per_thread) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    if (shots_per_thread < 0 || shots_per_thread > 2) return fail(BPQ_EINVAL, "shots per thread must be 0, 1 or 2");
+    if (shots_per_thread == 2 && !t->split)
+        return fail(BPQ_EINVAL, "two shots per thread need the split table layout (see bpq_tanner_layout)");
+    const int old = t->shots_per_thread;
+    t->shots_per_thread = shots_per_thread;
+    bpq::LaunchShape s;
+    int rc = bpq::decode_uses_pairs(t, BPQ_MOMENTUM, false) ? bpq::decode_pair_shape(t, BPQ_MOMENTUM, &s)
+                                                            : bpq::decode_launch_shape(t, -1, &s);
+    if (rc) t->shots_per_thread = old;
+    return rc;
+}
+
+int bpq_get_shots_per_thread(const bpq_tanner *t, int variant, int *shots_per_thread) {
+    if (!t || !shots_per_thread) return fail(BPQ_EINVAL, "NULL argument");
+    *shots_per_thread = bpq::decode_uses_pairs(t, variant, false) ? 2 : 1;
+    return BPQ_OK;
 }
 
 int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
@@ -580,25 +601,32 @@ int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
     if (B < 1) return fail(BPQ_EINVAL, "autotune needs a non-empty sample");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nodes = t->N > t->M ? t->N : t->M;
-    const int old_t = t->threads_per_shot, old_s = t->shots_per_cta;
-    int best_T = 0, best_S = 0;
+    const int old_t = t->threads_per_shot, old_s = t->shots_per_cta, old_k = t->shots_per_thread;
+    int best_T = 0, best_S = 0, best_K = 1;
     float best = 1e30f;
     cudaEvent_t e0, e1;
     rc = bpq::cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
     if (rc) return rc;
     rc = bpq::cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
     if (rc) { cudaEventDestroy(e0); return rc; }
-    // candidate shapes: 1..4 nodes per thread, about 128..512 threads per CTA
-    for (int npt = 1; npt <= bpq::kMaxNodesPerThread && !rc; ++npt) {
+    // candidate shapes: one or (split tables, not AEWA-BP) two shots per
+    // thread; 1..4 nodes per thread (1..2 with two shots per thread); 1..32
+    // shot groups per CTA
+    const bool can_pair = t->split && variant >= BPQ_PLAIN && variant <= BPQ_EWAINIT;
+    for (int K = 1; K <= (can_pair ? 2 : 1) && !rc; ++K)
+    for (int npt = 1; npt <= (K == 2 ? 2 : bpq::kMaxNodesPerThread) && !rc; ++npt) {
         const int T = (((nodes + npt - 1) / npt + 31) / 32) * 32;
         if (T > bpq::kMaxThreadsPerShot) continue;
         if (npt > 1 && (((nodes + npt - 2) / (npt - 1) + 31) / 32) * 32 == T) continue;  // same T as npt-1
-        for (int S : {1, 2, 4, 8, 15, 32}) {
+        for (int S : {1, 2, 4, 8, 15, 28, 32}) {
             if (S * T > (npt <= 2 ? 1024 : 512) || (S > 15 && T > 32) || (S > 1 && S * T < 64)) continue;
+            if ((K == 2 && S > bpq::kMaxPairGroupsPerCta) || (K == 1 && S == 28)) continue;
             t->threads_per_shot = T;
             t->shots_per_cta = S;
+            t->shots_per_thread = K;
             bpq::LaunchShape shape;
-            if (bpq::decode_launch_shape(t, variant, &shape)) continue;
+            if (K == 2 ? bpq::decode_pair_shape(t, variant, &shape) : bpq::decode_launch_shape(t, variant, &shape))
+                continue;
             float ms = 0.f;
             for (int rep = 0; rep < 3 && !rc; ++rep) {  // one warm-up, two timed
                 if (rep == 1) rc = bpq::cuda_check(cudaEventRecord(e0, st), "cudaEventRecord");
@@ -613,6 +641,7 @@ int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
                 best = ms / 2;
                 best_T = T;
                 best_S = S;
+                best_K = K;
             }
         }
     }
@@ -621,10 +650,12 @@ int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
     if (rc || best_T == 0) {
         t->threads_per_shot = old_t;
         t->shots_per_cta = old_s;
+        t->shots_per_thread = old_k;
         return rc ? rc : fail(BPQ_EINVAL, "no launch shape fits this code");
     }
     t->threads_per_shot = best_T;
     t->shots_per_cta = best_S;
+    t->shots_per_thread = best_K;
     if (threads_per_shot) *threads_per_shot = best_T;
     if (shots_per_cta) *shots_per_cta = best_S;
     if (best_ms) *best_ms = best;
@@ -634,7 +665,8 @@ int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
 int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_cta, int *ctas) {
     if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
     bpq::LaunchShape s;
-    int rc = bpq::decode_launch_shape(t, -1, &s);
+    int rc = bpq::decode_uses_pairs(t, BPQ_MOMENTUM, false) ? bpq::decode_pair_shape(t, BPQ_MOMENTUM, &s)
+                                                            : bpq::decode_launch_shape(t, -1, &s);
     if (rc) return rc;
     if (threads_per_shot) *threads_per_shot = s.T;
     if (shots_per_cta) *shots_per_cta = s.groups_per_cta;

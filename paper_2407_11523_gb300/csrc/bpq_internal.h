@@ -81,8 +81,9 @@ struct bpq_tanner {
     const uint8_t *d_logicals = nullptr;
     int num_sms = 0;
 
-    // launch preferences (0 = automatic)
-    int threads_per_shot = 0, shots_per_cta = 0;
+    // launch preferences (0 = automatic); with two shots per thread the
+    // first two describe a shot group (which decodes two shots at a time)
+    int threads_per_shot = 0, shots_per_cta = 0, shots_per_thread = 0;
 };
 
 namespace bpq {

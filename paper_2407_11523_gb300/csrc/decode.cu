@@ -23,7 +23,58 @@ DecodeKernelFn pick(int variant, int npt, bool trace, int layout) {
     return nullptr;
 }
 
+DecodeKernelFn pick_pair(int variant, int npt, int layout) {
+    const bool full = layout == 2;
+    switch (variant) {
+        case BPQ_PLAIN: return full ? pick_plain_pair_full(npt) : pick_plain_pair(npt);
+        case BPQ_MOMENTUM: return full ? pick_momentum_pair_full(npt) : pick_momentum_pair(npt);
+        case BPQ_ADAGRAD: return full ? pick_adagrad_pair_full(npt) : pick_adagrad_pair(npt);
+        case BPQ_EWAINIT: return full ? pick_ewainit_pair_full(npt) : pick_ewainit_pair(npt);
+    }
+    return nullptr;
+}
+
 }  // namespace
+
+bool decode_uses_pairs(const bpq_tanner *t, int variant, bool trace) {
+    if (trace || !t->split || variant < BPQ_PLAIN || variant > BPQ_EWAINIT) return false;
+    if (t->shots_per_thread == 1) return false;
+    if (t->shots_per_thread == 2) return true;
+    // automatic: where the stored launch shape fits two shots per thread
+    LaunchShape s;
+    const std::string keep = bpq_last_error();
+    const bool fits = decode_pair_shape(t, variant, &s) == BPQ_OK;
+    set_error(keep);
+    return fits;
+}
+
+int decode_pair_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
+    const int nodes = t->N > t->M ? t->N : t->M;
+    int T = t->threads_per_shot;
+    if (T <= 0) T = (((nodes + 1) / 2 + 31) / 32) * 32;  // two nodes per thread
+    if (T % 32 || T < 32 || T > kMaxThreadsPerShot)
+        return fail(BPQ_EINVAL, "threads per shot group must be a multiple of 32 in [32, 1024]");
+    const int npt = (nodes + T - 1) / T;
+    if (npt > 2) return fail(BPQ_EINVAL, "two shots per thread take at most two nodes per thread");
+    const int max_groups = T == 32 ? kMaxPairGroupsPerCta : 15;
+    int gpc = t->shots_per_cta;
+    if (gpc <= 0) gpc = 256 / T > 0 ? 256 / T : 1;  // about 256 threads per CTA
+    if (gpc > max_groups) gpc = max_groups;
+    while (gpc > 1 && gpc * T > 1024) --gpc;
+    s->T = T;
+    s->G = T / 32;
+    s->npt = npt;
+    s->groups_per_cta = gpc;
+    s->n_pad = (t->N + 3) & ~3;
+    s->slots_floats = (uint32_t)(4 * s->n_pad + 4);  // float2 slots
+    const int nstate = state_arrays(variant);
+    // per group: two vote words (16 bytes) | float2 slots | float2 state
+    s->group_bytes = (uint32_t)(16 + 8 * s->slots_floats + 8 * nstate * s->n_pad);
+    // table | Pi [3][n_pad] | initial messages [4 n_pad] | groups
+    s->smem = kSmemHeader + t->table.size() + (size_t)28 * s->n_pad + (size_t)gpc * s->group_bytes;
+    if (s->smem > 227 * 1024) return fail(BPQ_EINVAL, "shared memory of the launch shape exceeds 227 KB");
+    return BPQ_OK;
+}
 
 int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
     const int nodes = t->N > t->M ? t->N : t->M;
@@ -83,9 +134,10 @@ int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
 
 int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, cudaStream_t st, int *ctas_out) {
     LaunchShape s;
-    int rc = decode_launch_shape(t, variant, &s);
+    const bool pairs = decode_uses_pairs(t, variant, trace);
+    int rc = pairs ? decode_pair_shape(t, variant, &s) : decode_launch_shape(t, variant, &s);
     if (rc) return rc;
-    DecodeKernelFn fn = pick(variant, s.npt, trace, a.split);
+    DecodeKernelFn fn = pairs ? pick_pair(variant, s.npt, a.split) : pick(variant, s.npt, trace, a.split);
     if (!fn) return fail(BPQ_EINVAL, "no kernel for this variant (AEWA-BP has no trace mode)");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -94,7 +146,8 @@ int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, c
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, s.smem);
     if (e != cudaSuccess || per_sm < 1) return fail(BPQ_ECUDA, "launch shape does not fit on an SM");
     long ctas = (long)per_sm * t->num_sms;
-    const long need = (a.B + s.groups_per_cta - 1) / s.groups_per_cta;
+    const long per_cta = (long)s.groups_per_cta * (pairs ? 2 : 1);
+    const long need = (a.B + per_cta - 1) / per_cta;
     if (ctas > need) ctas = need;
     if (ctas < 1) ctas = 1;
     a.G = s.G;

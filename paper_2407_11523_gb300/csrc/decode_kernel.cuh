@@ -393,6 +393,28 @@ __device__ __forceinline__ void emit_v2c(const DecodeArgs &a, const ShotParams &
     }
 }
 
+// The posterior rules of Momentum-BP and AdaGrad-BP, written with explicit
+// round-to-nearest intrinsics so that every kernel that uses them (one shot
+// per thread, or two shots per thread in f32x2 lanes) rounds alike.
+//  eqs. (mombp1)-(mombp3): g = gamma g_prev + (1 - gamma)(Q_prev - Pi - S),
+//                           Q = Q_prev - alpha g
+__device__ __forceinline__ float momentum_g(const ShotParams &sp, float qp, float Pi, float S, float g_prev) {
+    const float grad = __fsub_rn(__fsub_rn(qp, Pi), S);
+    return __fmaf_rn(sp.gamma, g_prev, __fmul_rn(1.f - sp.gamma, grad));
+}
+__device__ __forceinline__ float momentum_q(const ShotParams &sp, float qp, float g) {
+    return __fmaf_rn(-sp.alpha, g, qp);
+}
+//  eq. (boost): g' = Q_prev - Pi - S, G += g'^2 (from t = 2, or from t = 1),
+//               Q = Q_prev - alpha g' / (sqrt(G) + eps)
+__device__ __forceinline__ float adagrad_gp(float qp, float Pi, float S) { return __fsub_rn(__fsub_rn(qp, Pi), S); }
+__device__ __forceinline__ float adagrad_G(float G, float gp, bool accumulate) {
+    return accumulate ? __fmaf_rn(gp, gp, G) : G;
+}
+__device__ __forceinline__ float adagrad_q(const ShotParams &sp, float qp, float gp, float G) {
+    return __fmaf_rn(-__fmul_rn(sp.alpha, gp), rcp(__fadd_rn(sqrt_approx(G), sp.eps)), qp);
+}
+
 // Per-thread adjacency of the owned checks and qubits of one code:
 // cs: the four message slots of each owned check (padding -> zero slot);
 // info: check Paulis (bits 0-7) | qubit Paulis (bits 8-15); pp: qubit
@@ -635,18 +657,16 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
                         } else if (VARIANT == BPQ_MOMENTUM) {
                             // eqs. (mombp1), (mombp2) with the gradient of (mombp3)
                             const float qp = state[w * Np + j];
-                            const float grad = qp - Pi[w] - S[w];
-                            const float g = sp.gamma * state[(3 + w) * Np + j] + (1.f - sp.gamma) * grad;
-                            Q[w] = qp - sp.alpha * g;
+                            const float g = momentum_g(sp, qp, Pi[w], S[w], state[(3 + w) * Np + j]);
+                            Q[w] = momentum_q(sp, qp, g);
                             state[w * Np + j] = Q[w];
                             state[(3 + w) * Np + j] = g;
                         } else {
                             // eq. (boost) from t = 2; G accumulates g'^2
                             const float qp = state[w * Np + j];
-                            const float gp = qp - Pi[w] - S[w];
-                            float Gs = state[(3 + w) * Np + j];
-                            if (t >= 2 || sp.ada_from1) Gs += gp * gp;
-                            Q[w] = t == 1 ? Pi[w] + S[w] : qp - sp.alpha * gp * rcp(sqrt_approx(Gs) + sp.eps);
+                            const float gp = adagrad_gp(qp, Pi[w], S[w]);
+                            const float Gs = adagrad_G(state[(3 + w) * Np + j], gp, t >= 2 || sp.ada_from1);
+                            Q[w] = t == 1 ? Pi[w] + S[w] : adagrad_q(sp, qp, gp, Gs);
                             state[w * Np + j] = Q[w];
                             state[(3 + w) * Np + j] = Gs;
                         }

@@ -88,8 +88,24 @@ DecodeKernelFn pick_ewainit_full(int npt);
 DecodeKernelFn pick_aewa(int npt, bool trace, bool split);
 DecodeKernelFn pick_aewa_full(int npt);
 BatchKernelFn pick_ewainit_batch(int npt);
+// Two shots per thread (decode_pair.cuh), split tables, npt in {1, 2}; the
+// _full functions for split tables without padding.
+DecodeKernelFn pick_plain_pair(int npt);
+DecodeKernelFn pick_plain_pair_full(int npt);
+DecodeKernelFn pick_momentum_pair(int npt);
+DecodeKernelFn pick_momentum_pair_full(int npt);
+DecodeKernelFn pick_adagrad_pair(int npt);
+DecodeKernelFn pick_adagrad_pair_full(int npt);
+DecodeKernelFn pick_ewainit_pair(int npt);
+DecodeKernelFn pick_ewainit_pair_full(int npt);
 
 int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
+// Whether bpq_decode runs the two-shots-per-thread kernel for this graph and
+// variant (split table layout, not AEWA-BP, not a trace), and its shape: a
+// shot group of s->T threads decodes two shots at a time.
+bool decode_uses_pairs(const bpq_tanner *t, int variant, bool trace);
+int decode_pair_shape(const bpq_tanner *t, int variant, LaunchShape *s);
+constexpr int kMaxPairGroupsPerCta = 28;  // two shot indices per group in the 256-byte header
 // Shape of a code inside the batched kernel (CTAs of kBatchThreads threads).
 int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
 

@@ -98,10 +98,44 @@ def test_rejects_bad_arguments(bpq):
 
 def test_launch_shapes(bpq):
     t = bpq.Tanner("toric", 15)
+    t.set_shots_per_thread(1)
+    assert t.shots_per_thread("ewainit") == 1
     assert t.launch() == (256, 1)
     t.set_launch(256, 2)
     assert t.launch() == (256, 2)
-    assert bpq.Tanner("planar", 5).launch()[0] == 32
+    p = bpq.Tanner("planar", 5)
+    p.set_shots_per_thread(1)
+    assert p.launch()[0] == 32
+
+
+def test_two_shots_per_thread_shapes(bpq):
+    """Split tables decode two shots per thread by default (two nodes per
+    thread, about 256 threads per CTA); AEWA-BP and the generic layout keep
+    one shot per thread."""
+    t = bpq.Tanner("toric", 15)
+    assert t.shots_per_thread("ewainit") == 2 and t.shots_per_thread("plain") == 2
+    assert t.shots_per_thread("aewa") == 1
+    assert t.launch() == (256, 1)
+    t.set_launch(480, 1)  # one node per thread
+    assert t.launch() == (480, 1)
+    t.set_launch(128, 1)  # four nodes per thread: only one shot per thread fits
+    assert t.shots_per_thread("ewainit") == 1
+    with pytest.raises(bpq.BPQError):
+        t.set_shots_per_thread(2)  # the stored shape has four nodes per thread
+    t.set_launch(0, 0)
+    t.set_shots_per_thread(2)
+    assert t.shots_per_thread("ewainit") == 2 and t.launch() == (256, 1)
+    with pytest.raises(bpq.BPQError):
+        t.set_launch(128, 1)
+    with pytest.raises(bpq.BPQError):
+        t.set_shots_per_thread(3)
+    assert bpq.Tanner("planar", 5).launch() == (32, 8)
+    H = bpq.Tanner("toric", 5).dense()
+    H[0, np.nonzero(H[0])[0][0]] = 2  # a Y entry: generic layout
+    g = bpq.Tanner(H=H)
+    assert g.shots_per_thread("ewainit") == 1
+    with pytest.raises(bpq.BPQError):
+        g.set_shots_per_thread(2)
 
 
 def test_default_params_follow_the_paper(bpq):
