@@ -403,9 +403,13 @@ def run_ours(args, rank, world):
     # profile (profiles/*.json), used only while the kernel's code (comments
     # and whitespace aside) still matches the profiled one.
     traffic = issue_pct = prof_rec = None
+    pair = t.shots_per_thread("ewainit") == 2
+    kname = "decode_pair_kernel" if pair else "decode_kernel"
     try:
-        prof_rec = json.load(open(os.path.join(ROOT, "profiles", "decode_kernel_toric15_ewainit.json")))
-        src = open(os.path.join(ROOT, "paper_2407_11523_gb300", "csrc", "decode_kernel.cuh")).read()
+        prof_rec = json.load(open(os.path.join(ROOT, "profiles", f"{kname}_toric15_ewainit.json")))
+        csrc = os.path.join(ROOT, "paper_2407_11523_gb300", "csrc")
+        src = "".join(open(os.path.join(csrc, f)).read()
+                      for f in (["decode_kernel.cuh", "decode_pair.cuh"] if pair else ["decode_kernel.cuh"]))
         if kernel_code_hash(src) == prof_rec["kernel_code_sha256_16"]:
             traffic = float(prof_rec["dram_bytes_per_shot"]) * args.shots_per_p
             issue_pct = float(prof_rec["issue_active_pct"])
@@ -432,7 +436,7 @@ def run_ours(args, rank, world):
     impl_achieved = impl_sfu_per_edge_update * eu_per_launch / kernel_sec
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": sfu_peak / 1e12, "unit": "TSFUop/s",
                 "frac": achieved / sfu_peak, "traffic": traffic,
-                "kernel": ("decode_pair_kernel<EWAINIT>" if t.shots_per_thread("ewainit") == 2 else "decode_kernel<EWAINIT>"), "per_unit": f"{sfu_per_edge_update:g} SFU ops per edge-update "
+                "kernel": f"{kname}<EWAINIT>", "per_unit": f"{sfu_per_edge_update:g} SFU ops per edge-update "
                 "(the literal form's tanh, atanh, softplus and log-sum-exp)",
                 "edge_updates_per_launch": eu_per_launch, "launch_ms": ew["launch_ms_mean"],
                 "impl_sfu_per_edge_update": impl_sfu_per_edge_update,

@@ -134,7 +134,21 @@ int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
 
 int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, cudaStream_t st, int *ctas_out) {
     LaunchShape s;
-    const bool pairs = decode_uses_pairs(t, variant, trace);
+    bool pairs = decode_uses_pairs(t, variant, trace);
+    if (pairs && t->shots_per_thread == 0) {
+        // automatic choice: pairing shots pays once the batch fills the GPU;
+        // a batch that one wave of one-shot groups takes at once finishes
+        // sooner with one shot per group (its latency is its slowest shot)
+        LaunchShape one;
+        int per_sm = 0;
+        DecodeKernelFn f1 = nullptr;
+        if (decode_launch_shape(t, variant, &one) == BPQ_OK && (f1 = pick(variant, one.npt, false, a.split)) &&
+            cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one.smem) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f1, one.T * one.groups_per_cta, one.smem) ==
+                cudaSuccess &&
+            (long)a.B <= (long)per_sm * t->num_sms * one.groups_per_cta)
+            pairs = false;
+    }
     int rc = pairs ? decode_pair_shape(t, variant, &s) : decode_launch_shape(t, variant, &s);
     if (rc) return rc;
     DecodeKernelFn fn = pairs ? pick_pair(variant, s.npt, a.split) : pick(variant, s.npt, trace, a.split);
