@@ -242,10 +242,12 @@ int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_ct
  * next shot from the queue as soon as its own shot stops (split table layout
  * only, see bpq_tanner_layout; plain, Momentum, AdaGrad and EWAInit BP; not
  * the trace, serial, batched or AEWA-BP paths); 0 = automatic (2 where it
- * applies and the batch is larger than one wave of one-shot groups, which
- * take a small batch at once and finish it sooner).  Per-shot results are
- * the same bit for bit either way.  bpq_get_shots_per_thread reports what
- * bpq_decode will use for `variant` on large batches.
+ * applies and the batch holds at least 128 shots per resident one-shot shot
+ * group, e.g. 77824 toric d = 15 shots on a GB300: a pair's iteration does two
+ * shots' work, so smaller batches, whose time is set by their slowest shots,
+ * finish sooner with one shot per thread).  Per-shot results are the same
+ * bit for bit either way.  bpq_get_shots_per_thread reports what bpq_decode
+ * will use for `variant` on large batches.
  * Errors: EINVAL (value outside 0..2, 2 on a table without the split
  * layout, a stored launch shape that does not fit). */
 int bpq_set_shots_per_thread(bpq_tanner *t, int shots_per_thread);

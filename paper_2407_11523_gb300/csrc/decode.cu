@@ -136,9 +136,12 @@ int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, c
     LaunchShape s;
     bool pairs = decode_uses_pairs(t, variant, trace);
     if (pairs && t->shots_per_thread == 0) {
-        // automatic choice: pairing shots pays once the batch fills the GPU;
-        // a batch that one wave of one-shot groups takes at once finishes
-        // sooner with one shot per group (its latency is its slowest shot)
+        // automatic choice: a pair's iteration does two shots' work, so a
+        // batch's tail (its slowest shots) runs longer; pairing pays only
+        // once each resident one-shot group would decode many shots.
+        // Measured on GB300 (EWAInit-BP): toric d = 15 pairs win from 65536
+        // shots, planar d = 25 from 16384, both about 100 shots per resident
+        // one-shot group; planar d = 9 breaks even at 262144 (172 per group)
         LaunchShape one;
         int per_sm = 0;
         DecodeKernelFn f1 = nullptr;
@@ -146,7 +149,7 @@ int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, c
             cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one.smem) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f1, one.T * one.groups_per_cta, one.smem) ==
                 cudaSuccess &&
-            (long)a.B <= (long)per_sm * t->num_sms * one.groups_per_cta)
+            (long)a.B < kPairShotsPerGroup * (long)per_sm * t->num_sms * one.groups_per_cta)
             pairs = false;
     }
     int rc = pairs ? decode_pair_shape(t, variant, &s) : decode_launch_shape(t, variant, &s);

@@ -106,6 +106,9 @@ int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
 bool decode_uses_pairs(const bpq_tanner *t, int variant, bool trace);
 int decode_pair_shape(const bpq_tanner *t, int variant, LaunchShape *s);
 constexpr int kMaxPairGroupsPerCta = 28;  // two shot indices per group in the 256-byte header
+// Automatic choice of two shots per thread: from this many shots per
+// resident one-shot group of the batch.
+constexpr long kPairShotsPerGroup = 128;
 // Shape of a code inside the batched kernel (CTAs of kBatchThreads threads).
 int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
 

@@ -503,11 +503,11 @@ def test_full_size_toric_d15_bench_configuration(bpq, p, k):
     R = robust
     assert R.mean() >= 0.88
     # as in test_gpu_sweep: strict on the robust shots the oracle converges,
-    # at most 1 % converging where the oracle runs to max_iter
+    # at most 0.5 % of the shots converging where the oracle runs to max_iter
     RC, RU = R & conv_r, R & ~conv_r
     assert (conv_c[:n] == 1)[RC].mean() >= 0.999
     assert ((fail_c[:n] > 0)[RC] == fail_r[RC]).mean() >= 0.999
-    assert (conv_c[:n] == 0)[RU].mean() >= 0.99
+    assert ((conv_c[:n] == 1) & RU).sum() <= 0.005 * n
     both = RC & (conv_c[:n] == 1)
     assert (row_hashes(est_head[both]) == g[key + "_est"][both]).mean() >= 0.995
 
