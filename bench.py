@@ -778,6 +778,11 @@ SERVE_CODES = [(k, d) for k in ("planar", "xzzx") for d in range(5, 32, 2)]
 
 
 def run_serve(args, rank, world):
+    """Poisson streams of single-shot requests over planar and XZZX codes
+    d = 5..31 at p = 0.05 (EWAInit-BP), served by the slot server (a
+    persistent kernel whose shot groups take the next request as soon as
+    they finish a shot) and by the lane server (micro-batches per stream)
+    for comparison; p50/p99 latency and shots/s per offered load."""
     import torch
 
     import paper_2407_11523_gb300 as bpq
@@ -787,10 +792,13 @@ def run_serve(args, rank, world):
     codes = [bpq.Tanner(*cd).upload() for cd in SERVE_CODES]
     priors = [bpq.prior_tensor(t, *ch) for t in codes]
     params = bpq.make_params("ewainit", alpha=0.5)
-    srv = bpq.Server(codes, priors, "ewainit", params=params, max_iter=MAX_ITER, n_lanes=4, max_batch=4096)
+    servers = {"slots": bpq.Server(codes, priors, "ewainit", params=params, max_iter=MAX_ITER, mode="slots",
+                                   slots_per_code=1024),
+               "lanes": bpq.Server(codes, priors, "ewainit", params=params, max_iter=MAX_ITER, n_lanes=4,
+                                   max_batch=4096)}
     rng = np.random.default_rng(SEED + 7)
     pool = {}
-    R_pool = 20000
+    R_pool = 200000
     code_pool = rng.integers(0, len(codes), size=R_pool)
     for c, t in enumerate(codes):
         n = int((code_pool == c).sum())
@@ -801,32 +809,48 @@ def run_serve(args, rank, world):
     for c in code_pool:
         syn_pool.append(pool[c][fill[c]])
         fill[c] += 1
-    results = []
-    srv.replay(code_pool[:2000], np.zeros(2000), syn_pool[:2000])  # warm-up
-    launches0 = srv.launches()
-    for load in [float(x) for x in args.loads.split(",")]:
-        R = int(min(R_pool, max(2000, load * 1.0)))
-        arrival = np.cumsum(rng.exponential(1.0 / load, size=R))
-        arrival -= arrival[0]
-        ests, conv, iters, done, used = srv.replay(code_pool[:R], arrival, syn_pool[:R])
-        lat = done - arrival
-        span = done.max() - arrival[0]
-        eu = sum(int(iters[r]) * codes[code_pool[r]].E for r in range(R))
-        results.append({"offered_per_s": load, "requests": R, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                        "p99_ms": float(np.percentile(lat, 99) * 1e3), "shots_per_s": R / span,
-                        "edge_updates_per_s": eu / span, "lanes_used": used,
-                        "converged_frac": float(conv.mean())})
+    out = {}
+    launches = 0
+    for name, srv in servers.items():
+        srv.replay(code_pool[:2000], np.zeros(2000), syn_pool[:2000])  # warm-up
+        launches0 = srv.launches()
+        results = []
+        for load in [float(x) for x in args.loads.split(",")]:
+            R = int(min(R_pool, max(2000, load * 0.02)))
+            arrival = np.cumsum(rng.exponential(1.0 / load, size=R))
+            arrival -= arrival[0]
+            ests, conv, iters, done, used = srv.replay(code_pool[:R], arrival, syn_pool[:R])
+            lat = done - arrival
+            span = done.max() - arrival[0]
+            eu = sum(int(iters[r]) * codes[code_pool[r]].E for r in range(R))
+            results.append({"offered_per_s": load, "requests": R, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                            "p99_ms": float(np.percentile(lat, 99) * 1e3), "shots_per_s": R / span,
+                            "edge_updates_per_s": eu / span,
+                            ("ctas" if name == "slots" else "lanes_used"): used,
+                            "converged_frac": float(conv.mean())})
+        # saturation: every request available at once
+        R = R_pool
+        ests, conv, iters, done, used = srv.replay(code_pool[:R], np.zeros(R), syn_pool[:R])
+        sat = R / done.max()
+        out[name] = {"loads": results, "saturation_shots_per_s": sat,
+                     "launches": srv.launches() - launches0}
+        launches += srv.launches() - launches0
     if rank == 0:
-        best = max(r["shots_per_s"] for r in results)
+        best = out["slots"]["saturation_shots_per_s"]
         line = {"metric": "serving: p50/p99 latency and shots/s under a Poisson request stream (continuous batching)",
-                "value": best, "unit": "shots/s", "n_gpus": world, "steps": len(results), "warmup": 1,
+                "value": best, "unit": "shots/s", "n_gpus": world, "steps": len(out["slots"]["loads"]), "warmup": 1,
                 "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "single-shot requests, planar and XZZX codes d = 5, 7, ..., 31 (uniform), "
-                                       "depolarising p = 0.05, EWAInit-BP alpha = 0.5, max_iter 100; 4 lanes x 4096 "
-                                       "shots of device budget; Poisson arrivals",
-                           "loads": results},
-                "gpu_launches": srv.launches() - launches0}
+                                       "depolarising p = 0.05, EWAInit-BP alpha = 0.5, max_iter 100; Poisson "
+                                       "arrivals; value = the slot server's saturation shots/s (200000 requests "
+                                       "available at once)",
+                           "slot_server": "1024 request slots per code in mapped host memory, one persistent "
+                                          "kernel (bpq_server_create_slots)",
+                           "lane_server": "4 lanes x 4096 shots of device budget, one batched launch per dispatch "
+                                          "(bpq_server_create)",
+                           "servers": out},
+                "gpu_launches": launches}
         print(json.dumps(line), flush=True)
 
 

@@ -374,9 +374,42 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
                       const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, uint8_t *conv_host,
                       uint8_t *iters_host, double *done_s, int *lanes_used);
 
-/* launches (may be NULL): the number of batched decode kernels the server
- * has launched since bpq_server_create (one per dispatch to a lane).
- * Errors: EINVAL. */
+/* Slot-granular continuous batching (an interface addition; the paper
+ * decodes offline batches).  A persistent kernel of resident CTAs decodes
+ * single-shot requests as they arrive: each code has a ring of
+ * slots_per_code request slots in mapped pinned host memory (allocated here
+ * and owned by the server); bpq_server_replay admits a request that has
+ * arrived into the next free slot of its code's ring (writing its syndrome
+ * there and publishing the code's request count with a release store), and a
+ * shot group that finishes a shot claims the next published request of its
+ * CTA's current code at once.  A CTA whose code has nothing to claim moves
+ * to another code with published requests (re-staging that code's
+ * adjacency).  Results come back through a completion queue in mapped
+ * memory, and a slot is free again once its result has been read, so the
+ * rings are the admission budget: at most n_codes x slots_per_code requests
+ * are in flight.  Every device-side wait is bounded: the kernel returns
+ * after about idle_timeout_us of finding nothing to claim, and replay
+ * relaunches it (a CUDA graph captured at creation) while requests remain.
+ * A request's result is the one bpq_decode gives for its syndrome alone.
+ * Plain, Momentum, AdaGrad or EWAInit BP.  dev_mem: at least
+ * bpq_server_slot_device_bytes(n_codes) of caller-owned device memory (the
+ * per-code descriptors, claim counters and status).  lanes_used of replay
+ * reports the serving grid's CTAs.  Errors: EINVAL, ESTATE, ECUDA (also a
+ * device-side bounded wait that gave up). */
+size_t bpq_server_slot_device_bytes(int n_codes);
+/* Counters of the slot server's last replay (for tuning): CTA code switches,
+ * scans that found no code with requests to claim, and claims that found
+ * the CTA's code empty.  Synchronizes.  Errors: EINVAL (not a slot server),
+ * ECUDA. */
+int bpq_server_slot_stats(bpq_server *s, long *code_switches, long *empty_scans, long *empty_claims);
+int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *priors_dev, int n_codes, int variant,
+                            const bpq_params *params, int max_iter, int slots_per_code, int idle_timeout_us,
+                            void *dev_mem, size_t dev_bytes, bpq_server **out);
+
+/* launches (may be NULL): the number of decode kernels the server has
+ * launched since its creation (lane server: one batched kernel per dispatch
+ * to a lane; slot server: one serving kernel per replay, plus one per
+ * relaunch after an idle period).  Errors: EINVAL. */
 int bpq_server_stats(const bpq_server *s, long *launches);
 
 void bpq_server_free(bpq_server *s);

@@ -84,6 +84,10 @@ def lib():
             "bpq_server_create": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, P, sz, PP]),
             "bpq_server_replay": (i, [P, i, P, P, P, P, P, P, P, P, P, pi]),
             "bpq_server_stats": (i, [P, ctypes.POINTER(ctypes.c_long)]),
+            "bpq_server_slot_device_bytes": (sz, [i]),
+            "bpq_server_slot_stats": (i, [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                                          ctypes.POINTER(ctypes.c_long)]),
+            "bpq_server_create_slots": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, P, sz, PP]),
             "bpq_server_free": (None, [P]),
             "bpq_train_workspace_bytes": (sz, [P, i, i, i, i]),
             "bpq_train_forward": (i, [P, i, P, P, P, i, i, i, P, P, P, P, ctypes.c_float, P, P, P, sz, P]),
@@ -455,22 +459,35 @@ class BatchPlan:
 
 
 class Server:
-    """Continuous-batching decoding server (bpq_server_*): n_lanes streams
-    with room for max_batch shots each; replay() serves a request trace in
-    real time and returns per-request outputs and completion times."""
+    """Decoding server (bpq_server_*); replay() serves a request trace in real
+    time and returns per-request outputs and completion times.
+
+    mode="lanes": n_lanes streams with room for max_batch shots each, each
+    dispatch a batched launch (bpq_server_create).  mode="slots": one
+    persistent kernel whose shot groups take the next request as soon as they
+    finish a shot, with slots_per_code request slots per code
+    (bpq_server_create_slots)."""
 
     def __init__(self, codes, priors, variant="ewainit", params=None, max_iter=100, n_lanes=4, max_batch=4096,
-                 **param_kw):
+                 mode="lanes", slots_per_code=1024, idle_timeout_us=200000, **param_kw):
         v = VARIANTS.get(variant, variant)
         self.params = params if params is not None else make_params(v, **param_kw)
         self.codes = [t.upload() for t in codes]
         self.priors = [p.contiguous() for p in priors]
+        self.mode = mode
         n = len(codes)
         harr = (ctypes.c_void_p * n)(*[t.handle.value for t in self.codes])
         parr = (ctypes.c_void_p * n)(*[p.data_ptr() for p in self.priors])
+        self._h = ctypes.c_void_p()
+        if mode == "slots":
+            nbytes = lib().bpq_server_slot_device_bytes(n)
+            self.mem = torch.empty(nbytes, dtype=torch.uint8, device=self.priors[0].device)
+            _check(lib().bpq_server_create_slots(harr, parr, n, v, ctypes.byref(self.params), max_iter,
+                                                 slots_per_code, idle_timeout_us, _ptr(self.mem), nbytes,
+                                                 ctypes.byref(self._h)), "bpq_server_create_slots")
+            return
         nbytes = lib().bpq_server_device_bytes(harr, n, n_lanes, max_batch)
         self.mem = torch.empty(nbytes, dtype=torch.uint8, device=self.priors[0].device)
-        self._h = ctypes.c_void_p()
         _check(lib().bpq_server_create(harr, parr, n, v, ctypes.byref(self.params), max_iter, n_lanes, max_batch,
                                        _ptr(self.mem), nbytes, ctypes.byref(self._h)), "bpq_server_create")
 
@@ -499,8 +516,16 @@ class Server:
         ests = [est[o:o + n] for o, n in zip(est_off, Ns)]
         return ests, conv[:R], iters[:R], done[:R], used.value
 
+    def slot_stats(self):
+        """Slot server counters of the last replay: (code switches, empty
+        scans, empty claims)."""
+        a, b, c = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        _check(lib().bpq_server_slot_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "bpq_server_slot_stats")
+        return a.value, b.value, c.value
+
     def launches(self):
-        """Batched decode kernels launched since creation."""
+        """Decode kernels launched since creation."""
         n = ctypes.c_long()
         _check(lib().bpq_server_stats(self._h, ctypes.byref(n)), "bpq_server_stats")
         return n.value

@@ -482,8 +482,11 @@ __device__ __forceinline__ GroupMem group_mem(const DecodeArgs &a, uint8_t *base
 // decision satisfies the syndrome or max_iter is reached; writes the shot's
 // outputs.  npt <= NPT is the number of nodes each thread owns.  FULL
 // (split layout only): every check has four edges and every qubit two X and
-// two Z edges, so no edge is padding.
-template <int VARIANT, int NPT, bool TRACE, bool SPLIT, bool FULL>
+// two Z edges, so no edge is padding.  STAGED: a.syn, a.est, a.conv and
+// a.iters may point into shared memory (the serving kernel stages each
+// request's syndrome and outputs there), so the syndrome words are read with
+// a generic load instead of the read-only global path.
+template <int VARIANT, int NPT, bool TRACE, bool SPLIT, bool FULL, bool STAGED = false>
 __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<NPT> &adj, const GroupMem &m,
                                            int npt, int T, int tg, int G, int bar_id, int shot, float alpha) {
     const ShotParams sp = shot_params<PhiForm<VARIANT>::value>(a, alpha);
@@ -498,7 +501,8 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
     for (int k = 0; k < NPT; ++k) {
         const int i = k * T + tg;
         if (k < npt && i < M) {
-            const uint32_t w = __ldg(a.syn + (size_t)shot * a.W + (i >> 5));
+            const uint32_t *src = a.syn + (size_t)shot * a.W + (i >> 5);
+            const uint32_t w = STAGED ? *reinterpret_cast<const volatile uint32_t *>(src) : __ldg(src);
             sbits |= ((w >> (i & 31)) & 1u) << k;
         }
     }
