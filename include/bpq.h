@@ -253,6 +253,17 @@ int bpq_get_launch(const bpq_tanner *t, int *threads_per_shot, int *shots_per_ct
 int bpq_set_shots_per_thread(bpq_tanner *t, int shots_per_thread);
 int bpq_get_shots_per_thread(const bpq_tanner *t, int variant, int *shots_per_thread);
 
+/* Bounds-checked decoding (a test aid; the paper has no counterpart): with
+ * on != 0, bpq_decode and bpq_decode_host run copies of the decode kernels
+ * compiled with checks on every shared-memory layout, slot index, table
+ * offset and output index.  A failed check sets the device error word that
+ * bpq_decode_status reads (value 5), substitutes a safe index and carries on
+ * (or, for a layout that does not fit, makes the CTA return before its first
+ * barrier); nothing traps.  Results are those of the unchecked kernels when
+ * every check passes.  Plain, Momentum, AdaGrad and EWAInit BP, at most two
+ * nodes per thread; other launches return EINVAL while it is on. */
+int bpq_set_debug_checks(bpq_tanner *t, int on);
+
 /* Autotuner of the launch shape (an addition; the paper has no GPU design):
  * times bpq_decode on the caller's sample batch (same arguments as
  * bpq_decode) for every candidate shape - one or two shots per thread, 1..4

@@ -72,6 +72,7 @@ def lib():
                                  ctypes.POINTER(ctypes.c_float)]),
             "bpq_get_launch": (i, [P, pi, pi, pi]),
             "bpq_set_shots_per_thread": (i, [P, i]),
+            "bpq_set_debug_checks": (i, [P, i]),
             "bpq_get_shots_per_thread": (i, [P, i, pi]),
             "bpq_check_logical": (i, [P, P, P, i, P, P]),
             "bpq_probe_peak": (i, [i, i, i, i, P, P]),
@@ -223,6 +224,10 @@ class Tanner:
         """1: one shot per thread; 2: two shots per thread (split tables);
         0: automatic (bpq_set_shots_per_thread)."""
         _check(lib().bpq_set_shots_per_thread(self._h, k), "bpq_set_shots_per_thread")
+
+    def set_debug_checks(self, on=True):
+        """Run the bounds-checked decode kernels (bpq_set_debug_checks)."""
+        _check(lib().bpq_set_debug_checks(self._h, 1 if on else 0), "bpq_set_debug_checks")
 
     def shots_per_thread(self, variant="ewainit") -> int:
         k = ctypes.c_int()

@@ -586,6 +586,12 @@ int bpq_set_shots_per_thread(bpq_tanner *t, int shots_per_thread) {
     return rc;
 }
 
+int bpq_set_debug_checks(bpq_tanner *t, int on) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    t->debug_checks = on != 0;
+    return BPQ_OK;
+}
+
 int bpq_get_shots_per_thread(const bpq_tanner *t, int variant, int *shots_per_thread) {
     if (!t || !shots_per_thread) return fail(BPQ_EINVAL, "NULL argument");
     *shots_per_thread = bpq::decode_uses_pairs(t, variant, false) ? 2 : 1;

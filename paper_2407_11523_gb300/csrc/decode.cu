@@ -154,7 +154,15 @@ int decode_launch(const bpq_tanner *t, DecodeArgs &a, int variant, bool trace, c
     }
     int rc = pairs ? decode_pair_shape(t, variant, &s) : decode_launch_shape(t, variant, &s);
     if (rc) return rc;
-    DecodeKernelFn fn = pairs ? pick_pair(variant, s.npt, a.split) : pick(variant, s.npt, trace, a.split);
+    DecodeKernelFn fn = nullptr;
+    if (t->debug_checks) {
+        fn = trace ? nullptr : pick_debug(variant, s.npt, pairs, a.split);
+        if (!fn)
+            return fail(BPQ_EINVAL, "no bounds-checked kernel for this launch (plain, Momentum, AdaGrad or EWAInit BP, "
+                                    "at most two nodes per thread, not a trace)");
+    } else {
+        fn = pairs ? pick_pair(variant, s.npt, a.split) : pick(variant, s.npt, trace, a.split);
+    }
     if (!fn) return fail(BPQ_EINVAL, "no kernel for this variant (AEWA-BP has no trace mode)");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));

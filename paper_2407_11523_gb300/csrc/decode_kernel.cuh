@@ -44,6 +44,15 @@
 // edges: the edge type is fixed by its position, so no per-edge Pauli
 // selects) and FULL (split tables without padding, e.g. the toric codes: no
 // zero/trash slot choice, no unused positions, no check-side clip).
+//
+// Bounds-checked build: with BPQ_DEBUG defined (decode_debug_*.cu compile
+// these headers a second time, into namespace dk_debug), every CTA checks its
+// launch's shared-memory layout against the dynamic shared memory it got,
+// every thread checks the slot indices and table offsets of the nodes it
+// loads, and every output write checks its index.  A failed check sets the
+// device error word (work[1] = 5) and substitutes a safe index (the zero slot,
+// or no write); a CTA whose layout does not fit returns before its first
+// barrier.  Nothing traps.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -53,6 +62,26 @@
 
 namespace bpq {
 namespace dk {
+
+// Error word value of a failed bounds check (BPQ_DEBUG builds).
+constexpr uint32_t kBoundsError = 5u;
+
+#ifdef BPQ_DEBUG
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+    uint32_t v;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+// true when idx < limit; else records the failure in the error word
+__device__ __forceinline__ bool bpq_in_bounds(size_t idx, size_t limit, uint32_t *err) {
+    if (idx < limit) return true;
+    atomicExch(err, kBoundsError);
+    return false;
+}
+#define BPQ_IN_BOUNDS(idx, limit, err) ::bpq::dk::bpq_in_bounds((size_t)(idx), (size_t)(limit), (err))
+#else
+#define BPQ_IN_BOUNDS(idx, limit, err) true
+#endif
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -434,14 +463,21 @@ __device__ __forceinline__ void load_adjacency(const DecodeArgs &a, const uint8_
         adj.info[k] = 0u;
         adj.pp[k] = 0u;
         const int i = k * T + tg;
-        if (k < npt && i < a.M) {
+        if (k < npt && i < a.M && BPQ_IN_BOUNDS(8 * i + 7, a.table_bytes, a.work + 1) &&
+            BPQ_IN_BOUNDS(a.off_chk_pauli + i, a.table_bytes, a.work + 1)) {
             const uint2 s = *reinterpret_cast<const uint2 *>(tab + 8 * i);
-            const uint32_t s0 = s.x & 0xFFFFu, s1 = s.x >> 16, s2 = s.y & 0xFFFFu, s3 = s.y >> 16;
+            uint32_t s0 = s.x & 0xFFFFu, s1 = s.x >> 16, s2 = s.y & 0xFFFFu, s3 = s.y >> 16;
+#ifdef BPQ_DEBUG
+            // a slot index is an edge slot (< 4 n_pad) or no slot
+            uint32_t *sv[4] = {&s0, &s1, &s2, &s3};
+            for (int n = 0; n < 4; ++n)
+                if (*sv[n] != kNoSlot && !BPQ_IN_BOUNDS(*sv[n], kZero, a.work + 1)) *sv[n] = kNoSlot;
+#endif
             adj.cs_lo[k] = (s0 == kNoSlot ? kZero : s0) | ((s1 == kNoSlot ? kZero : s1) << 16);
             adj.cs_hi[k] = (s2 == kNoSlot ? kZero : s2) | ((s3 == kNoSlot ? kZero : s3) << 16);
             adj.info[k] = tab[a.off_chk_pauli + i];
         }
-        if (k < npt && i < a.N) {
+        if (k < npt && i < a.N && BPQ_IN_BOUNDS(a.off_var_pauli + i, a.table_bytes, a.work + 1)) {
             const uint32_t vp = tab[a.off_var_pauli + i];
             adj.info[k] |= vp << 8;
             adj.pp[k] = (vp & 3u) | (((vp >> 2) & 3u) << 8) | (((vp >> 4) & 3u) << 16) | (((vp >> 6) & 3u) << 24);
@@ -705,10 +741,11 @@ __device__ __forceinline__ int decode_shot(const DecodeArgs &a, const ThreadAdj<
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             const int j = k * T + tg;
-            if (k < npt && j < N) a.est[(size_t)shot * N + j] = (uint8_t)dk[k];
+            if (k < npt && j < N && BPQ_IN_BOUNDS((size_t)shot * N + j, (size_t)a.B * N, a.work + 1))
+                a.est[(size_t)shot * N + j] = (uint8_t)dk[k];
         }
     }
-    if (tg == 0 && (!TRACE || a.conv)) {
+    if (tg == 0 && (!TRACE || a.conv) && BPQ_IN_BOUNDS(shot, a.B, a.work + 1)) {
         a.conv[shot] = (uint8_t)conv;
         a.iters[shot] = (uint8_t)iters;
     }
@@ -731,6 +768,21 @@ __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const 
     const int tg = tid - group * T;
     const int bar_id = 1 + group;
     const GroupMem m = group_mem(a, tab, group);
+#ifdef BPQ_DEBUG
+    // the launch's layout fits the dynamic shared memory (uniform across the
+    // CTA, so an early return happens before any barrier)
+    {
+        const size_t need = kSmemHeader + (size_t)a.table_bytes + (size_t)12 * a.n_pad +
+                            (size_t)(blockDim.x / T) * a.group_bytes;
+        const bool ok = need <= dynamic_smem_bytes() && a.n_pad >= a.N && a.slots_floats >= 4u * a.n_pad + 2u &&
+                        a.group_bytes >= 4u * (a.slots_floats + (uint32_t)StateArrays<VARIANT>::n * a.n_pad) &&
+                        (a.off_var_pauli + (uint32_t)a.N <= a.table_bytes);
+        if (!ok) {
+            if (tid == 0) atomicExch(a.work + 1, kBoundsError);
+            return;
+        }
+    }
+#endif
 
     // ---- stage the adjacency table once per CTA (bulk TMA copy) ----
     if (tid == 0) {

@@ -99,6 +99,10 @@ DecodeKernelFn pick_adagrad_pair_full(int npt);
 DecodeKernelFn pick_ewainit_pair(int npt);
 DecodeKernelFn pick_ewainit_pair_full(int npt);
 
+// Bounds-checked kernels (decode_debug.cu; bpq_set_debug_checks): npt in
+// {1, 2}, pairs on split layouts; nullptr where none is compiled.
+DecodeKernelFn pick_debug(int variant, int npt, bool pairs, int layout);
+
 int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s);
 // Whether bpq_decode runs the two-shots-per-thread kernel for this graph and
 // variant (split table layout, not AEWA-BP, not a trace), and its shape: a

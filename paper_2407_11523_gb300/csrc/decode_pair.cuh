@@ -257,9 +257,10 @@ __device__ __forceinline__ void decode_pairs(const DecodeArgs &a, const ThreadAd
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
                     const int j = k * T + tg;
-                    if (j < N) a.est[(size_t)shot[l] * N + j] = (uint8_t)((dk[k] >> (8 * l)) & 0xFFu);
+                    if (j < N && BPQ_IN_BOUNDS((size_t)shot[l] * N + j, (size_t)a.B * N, a.work + 1))
+                        a.est[(size_t)shot[l] * N + j] = (uint8_t)((dk[k] >> (8 * l)) & 0xFFu);
                 }
-                if (tg == 0) {
+                if (tg == 0 && BPQ_IN_BOUNDS(shot[l], a.B, a.work + 1)) {
                     a.conv[shot[l]] = conv ? 1 : 0;
                     a.iters[shot[l]] = (uint8_t)(conv ? t[l] - 1 : sp.max_iter);
                     grp_shot[l] = (int)atomicAdd(a.work, 1u);
@@ -359,6 +360,20 @@ __global__ void __launch_bounds__(1024, 1) decode_pair_kernel(const DecodeArgs a
     const int tg = tid - group * T;
     const int bar_id = 1 + group;
     const PairMem m = pair_mem(a, tab, group);
+#ifdef BPQ_DEBUG
+    {
+        const size_t need = kSmemHeader + (size_t)a.table_bytes + (size_t)28 * a.n_pad +
+                            (size_t)(blockDim.x / T) * a.group_bytes;
+        const bool ok = need <= dynamic_smem_bytes() && a.n_pad >= a.N && a.slots_floats >= 4u * a.n_pad + 2u &&
+                        a.group_bytes >= kPairVoteBytes + 8u * (a.slots_floats +
+                                                               (uint32_t)StateArrays<VARIANT>::n * a.n_pad) &&
+                        (a.off_var_pauli + (uint32_t)a.N <= a.table_bytes) && blockDim.x / T <= kMaxPairGroupsPerCta;
+        if (!ok) {
+            if (tid == 0) atomicExch(a.work + 1, kBoundsError);
+            return;
+        }
+    }
+#endif
 
     // ---- stage the adjacency table once per CTA (bulk TMA copy) ----
     if (tid == 0) {
