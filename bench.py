@@ -538,13 +538,15 @@ def run_mixed(args, rank, world):
             groups.append((cd, noise_name, B))
             k += 1
     params = bpq.make_params("ewainit", alpha=0.5)
-    # autotune each code's launch shape on its largest sample
-    shapes = {}
+    # autotune each code's launch shape, one-code and batched, on its largest sample
+    shapes, batch_shapes = {}, {}
     for cd in MIX_CODES:
         t = tanners[cd]
         best = max((it for it in items if it[0] is t), key=lambda it: it[1].shape[0])
         sample = best[1][: min(8192, best[1].shape[0])].contiguous()
         shapes[f"{cd[0]} d={cd[1]}"] = bpq.autotune(t, sample, best[2], "ewainit", params=params, max_iter=MAX_ITER)
+        bpq.autotune_batch(t, sample, best[2], "ewainit", params=params, max_iter=MAX_ITER)
+        batch_shapes[f"{cd[0]} d={cd[1]}"] = t.batch_launch("ewainit")
     work = bpq.workspace(dev)
     outs = [(torch.empty((it[1].shape[0], it[0].N), dtype=torch.uint8, device=dev),
              torch.empty(it[1].shape[0], dtype=torch.uint8, device=dev),
@@ -608,7 +610,7 @@ def run_mixed(args, rank, world):
                                        "EWAInit-BP alpha=0.5, max_iter 100",
                            "groups": [{"code": f"{cd[0]} d={cd[1]}", "noise": nn, "shots": B, "ler": e}
                                       for (cd, nn, B), e in zip(groups, errs)],
-                           "launch_shapes": shapes, "batch_plan": plan.info()},
+                           "launch_shapes": shapes, "batch_shapes": batch_shapes, "batch_plan": plan.info()},
                 "edge_updates_per_s": reduce_sum(float(edge_updates), world) / sec,
                 "compare_shots_per_s": {kk: shots / v for kk, v in res.items()},
                 "batched_equals_per_code": identical,

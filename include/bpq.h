@@ -310,13 +310,13 @@ int bpq_decode_serial_trace(const bpq_tanner *t, const uint32_t *syn_dev, const 
  * decodes one code at a time).  Each item is one code's batch: syndromes,
  * prior and outputs exactly as for bpq_decode.  All items share the variant
  * (plain, Momentum, AdaGrad or EWAInit BP), parameters and max_iter.  A CTA
- * of 1024 threads works on one item at a time with that code's
- * threads-per-shot (from bpq_set_launch / bpq_autotune, else the default;
- * at most two nodes per thread): its shot groups take the item's shots one
- * by one from a per-item counter until none are left, and the CTA then moves
- * to another item with shots left, re-staging that code's adjacency.  CTAs
- * start spread over the items in proportion to shots x edges.  Per-shot
- * results equal those of bpq_decode bit for bit. */
+ * of 1024 threads (at 64 registers a thread, the whole register file of an
+ * SM) works on one item at a time, split into that code's shot groups (see
+ * bpq_set_batch_launch): they take the item's shots one by one from a
+ * per-item counter until none are left, and the CTA then moves to another
+ * item with shots left, re-staging that code's adjacency.  CTAs start
+ * spread over the items in proportion to shots x edges.  Per-shot results
+ * equal those of bpq_decode bit for bit. */
 typedef struct {
     const bpq_tanner *tanner;  /* uploaded; all items on one device */
     const uint32_t *syn_dev;   /* [B][ceil(M/32)] */
@@ -345,10 +345,37 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
  * captured in a CUDA graph).  Runs of one plan must not overlap. */
 int bpq_batch_launch(const bpq_batch *b, void *stream);
 
-/* ctas: CTAs per launch; items: n_items; npt_max: the kernel's nodes per
- * thread; shots: total shots.  Any pointer may be NULL. */
+/* ctas: CTAs per launch; items: n_items; npt_max: the largest nodes per
+ * thread of an item; shots: total shots.  Any pointer may be NULL. */
 int bpq_batch_info(const bpq_batch *b, int *ctas, int *items, int *npt_max, long *shots);
 void bpq_batch_free(bpq_batch *b);
+
+/* Shape of a code inside the batched kernel and the servers (an
+ * implementation choice; the paper has no GPU design), stored in the handle
+ * and read when a plan or server is built: nodes_per_thread 1 or 2 sets the
+ * threads per shot group (max(N, M) / nodes_per_thread rounded up to a
+ * multiple of 32, at most 1024), and the CTA holds as many groups as fit in
+ * its 1024 threads (at most 15 multi-warp or 32 one-warp groups) and in
+ * 227 KB of shared memory.  0 = automatic: the choice that keeps the most
+ * node slots of a CTA busy (groups x max(N, M) / (nodes_per_thread x 1024)),
+ * two nodes per thread on a tie.  Independent of bpq_set_launch.
+ * Errors: EINVAL (a value outside 0..2, or a shape that does not fit).
+ * bpq_get_batch_launch reports the shape for `variant` (any output pointer
+ * may be NULL). */
+int bpq_set_batch_launch(bpq_tanner *t, int nodes_per_thread);
+int bpq_get_batch_launch(const bpq_tanner *t, int variant, int *threads_per_shot, int *shots_per_cta,
+                         int *nodes_per_thread);
+
+/* Autotuner of bpq_set_batch_launch: times a one-item plan of the caller's
+ * sample (arguments as bpq_decode; work_dev at least
+ * bpq_batch_workspace_bytes(1) bytes) with one and with two nodes per
+ * thread, and stores the faster in the handle.  Synchronizes `stream`; the
+ * outputs are those of the last trial.  Reports the choice and its time per
+ * launch (any output pointer may be NULL). */
+int bpq_autotune_batch(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+                       const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
+                       uint8_t *iters_dev, void *work_dev, size_t work_bytes, void *stream,
+                       int *nodes_per_thread, float *best_ms);
 
 /* ---------------------------------------------------------------- serving */
 

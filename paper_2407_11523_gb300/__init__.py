@@ -8,7 +8,8 @@ this package is its thin Python binding.
 """
 from ._binding import (  # noqa: F401
     ADAGRAD, AEWA, CODES, EWAINIT, MOMENTUM, PLAIN, PLANAR, TORIC, VARIANTS, XZZX,
-    BPQError, BatchPlan, Params, Server, Tanner, autotune, check_logical, decode, decode_host, decode_host_bytes, decode_status,
+    BPQError, BatchPlan, Params, Server, Tanner, autotune, autotune_batch, check_logical, decode, decode_host,
+    decode_host_bytes, decode_status,
     decode_trace, default_params, lib, make_params, prior_rows, prior_tensor, probe_peak, sample, unrolled_loss,
     unrolled_posterior, workspace,
 )

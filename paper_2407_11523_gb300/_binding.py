@@ -71,6 +71,10 @@ def lib():
             "bpq_autotune": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, P, pi, pi,
                                  ctypes.POINTER(ctypes.c_float)]),
             "bpq_get_launch": (i, [P, pi, pi, pi]),
+            "bpq_set_batch_launch": (i, [P, i]),
+            "bpq_get_batch_launch": (i, [P, i, pi, pi, pi]),
+            "bpq_autotune_batch": (i, [P, P, P, i, ctypes.POINTER(Params), i, i, P, P, P, P, sz, P, pi,
+                                       ctypes.POINTER(ctypes.c_float)]),
             "bpq_set_shots_per_thread": (i, [P, i]),
             "bpq_set_debug_checks": (i, [P, i]),
             "bpq_get_shots_per_thread": (i, [P, i, pi]),
@@ -220,6 +224,19 @@ class Tanner:
         _check(lib().bpq_get_launch(self._h, ctypes.byref(t), ctypes.byref(s), ctypes.byref(c)), "bpq_get_launch")
         return t.value, s.value
 
+    def set_batch_launch(self, nodes_per_thread=0):
+        """Nodes per thread (1 or 2; 0 = automatic) of this code inside the
+        batched kernel and the servers (bpq_set_batch_launch)."""
+        _check(lib().bpq_set_batch_launch(self._h, nodes_per_thread), "bpq_set_batch_launch")
+
+    def batch_launch(self, variant="ewainit"):
+        """(threads per shot group, groups per CTA, nodes per thread) inside
+        the batched kernel (bpq_get_batch_launch)."""
+        t, s, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().bpq_get_batch_launch(self._h, VARIANTS.get(variant, variant), ctypes.byref(t), ctypes.byref(s),
+                                          ctypes.byref(n)), "bpq_get_batch_launch")
+        return t.value, s.value, n.value
+
     def set_shots_per_thread(self, k=0):
         """1: one shot per thread; 2: two shots per thread (split tables);
         0: automatic (bpq_set_shots_per_thread)."""
@@ -253,6 +270,28 @@ def autotune(tanner: Tanner, syn, prior, variant="ewainit", params=None, max_ite
                               _ptr(conv), _ptr(iters), _ptr(work), _stream(stream), ctypes.byref(t_),
                               ctypes.byref(s_), ctypes.byref(ms)), "bpq_autotune")
     return t_.value, s_.value, ms.value
+
+
+def autotune_batch(tanner: Tanner, syn, prior, variant="ewainit", params=None, max_iter=100, stream=None,
+                   **param_kw):
+    """Time a one-item batched plan of this sample with one and with two
+    nodes per thread and keep the faster in the handle
+    (bpq_autotune_batch); returns (nodes_per_thread, ms)."""
+    tanner.upload()
+    v = VARIANTS.get(variant, variant)
+    p = params if params is not None else make_params(v, **param_kw)
+    B = syn.shape[0]
+    dev = syn.device
+    est = torch.empty((B, tanner.N), dtype=torch.uint8, device=dev)
+    conv = torch.empty(B, dtype=torch.uint8, device=dev)
+    iters = torch.empty(B, dtype=torch.uint8, device=dev)
+    nbytes = lib().bpq_batch_workspace_bytes(1)
+    work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    n_, ms = ctypes.c_int(), ctypes.c_float()
+    _check(lib().bpq_autotune_batch(tanner.handle, _ptr(syn), _ptr(prior), v, ctypes.byref(p), max_iter, B,
+                                    _ptr(est), _ptr(conv), _ptr(iters), _ptr(work), nbytes, _stream(stream),
+                                    ctypes.byref(n_), ctypes.byref(ms)), "bpq_autotune_batch")
+    return n_.value, ms.value
 
 
 def workspace(device=None) -> torch.Tensor:

@@ -18,7 +18,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "batch.cu", "server.cu", "train.cu", "decode.cu", "decode_plain.cu", "decode_momentum.cu", "decode_adagrad.cu",
            "decode_ewainit.cu", "decode_aewa.cu", "decode_plain_full.cu", "decode_momentum_full.cu",
            "decode_adagrad_full.cu", "decode_ewainit_full.cu", "decode_aewa_full.cu", "decode_plain_pair.cu",
-           "decode_momentum_pair.cu", "decode_adagrad_pair.cu", "decode_ewainit_pair.cu", "serve_kernels.cu",
+           "decode_momentum_pair.cu", "decode_adagrad_pair.cu", "decode_ewainit_pair.cu", "decode_plain_batch.cu",
+           "decode_momentum_batch.cu", "decode_adagrad_batch.cu", "decode_ewainit_batch.cu", "serve_kernels.cu",
            "decode_debug.cu", "serial.cu", "tanner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

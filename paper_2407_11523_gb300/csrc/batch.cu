@@ -27,12 +27,12 @@ struct bpq_batch {
 
 namespace bpq {
 
-BatchKernelFn pick_batch_kernel(int variant, int npt) {
+BatchKernelFn pick_batch_kernel(int variant, bool generic) {
     switch (variant) {
-        case BPQ_PLAIN: return pick_plain_batch(npt);
-        case BPQ_MOMENTUM: return pick_momentum_batch(npt);
-        case BPQ_ADAGRAD: return pick_adagrad_batch(npt);
-        case BPQ_EWAINIT: return pick_ewainit_batch(npt);
+        case BPQ_PLAIN: return pick_plain_batch(generic);
+        case BPQ_MOMENTUM: return pick_momentum_batch(generic);
+        case BPQ_ADAGRAD: return pick_adagrad_batch(generic);
+        case BPQ_EWAINIT: return pick_ewainit_batch(generic);
     }
     return nullptr;
 }
@@ -93,6 +93,7 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
     std::vector<double> weight(n_items);
     size_t smem = 0;
     int npt_max = 1;
+    bool generic = false;  // some item uses the generic table layout
     long useful_ctas = 0;  // CTAs that the items can keep busy at once
     for (int g = 0; g < n_items; ++g) {
         const bpq_tanner *t = items[g].tanner;
@@ -113,13 +114,14 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
         a.npt = s.npt;
         a.groups_per_cta = s.groups_per_cta;
         npt_max = std::max(npt_max, s.npt);
+        generic = generic || a.split == 0;
         smem = std::max(smem, s.smem);
         weight[g] = (double)items[g].B * t->E;
         useful_ctas += (items[g].B + s.groups_per_cta - 1) / s.groups_per_cta;
     }
     if (smem > 227 * 1024) return fail(BPQ_EINVAL, "a code of the batch needs more than 227 KB of shared memory");
 
-    bpq::BatchKernelFn fn = bpq::pick_batch_kernel(variant, npt_max);
+    bpq::BatchKernelFn fn = bpq::pick_batch_kernel(variant, generic);
     if (!fn) return fail(BPQ_EINVAL, "no batched kernel for this shape");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -186,5 +188,82 @@ int bpq_batch_info(const bpq_batch *b, int *ctas, int *items, int *npt_max, long
 }
 
 void bpq_batch_free(bpq_batch *b) { delete b; }
+
+int bpq_set_batch_launch(bpq_tanner *t, int nodes_per_thread) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    if (nodes_per_thread < 0 || nodes_per_thread > 2) return fail(BPQ_EINVAL, "nodes per thread must be 0, 1 or 2");
+    const int old = t->batch_nodes_per_thread;
+    t->batch_nodes_per_thread = nodes_per_thread;
+    bpq::LaunchShape s;
+    int rc = bpq::decode_batch_shape(t, BPQ_MOMENTUM, &s);
+    if (rc) t->batch_nodes_per_thread = old;
+    return rc;
+}
+
+int bpq_get_batch_launch(const bpq_tanner *t, int variant, int *threads_per_shot, int *shots_per_cta,
+                         int *nodes_per_thread) {
+    if (!t) return fail(BPQ_EINVAL, "tanner is NULL");
+    if (variant < BPQ_PLAIN || variant > BPQ_EWAINIT)
+        return fail(BPQ_EINVAL, "the batched kernel takes plain, Momentum, AdaGrad or EWAInit BP");
+    bpq::LaunchShape s;
+    int rc = bpq::decode_batch_shape(t, variant, &s);
+    if (rc) return rc;
+    if (threads_per_shot) *threads_per_shot = s.T;
+    if (shots_per_cta) *shots_per_cta = s.groups_per_cta;
+    if (nodes_per_thread) *nodes_per_thread = s.npt;
+    return BPQ_OK;
+}
+
+int bpq_autotune_batch(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
+                       const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
+                       uint8_t *iters_dev, void *work_dev, size_t work_bytes, void *stream, int *nodes_per_thread,
+                       float *best_ms) {
+    int rc = bpq::need_uploaded(t);
+    if (rc) return rc;
+    if (B < 1) return fail(BPQ_EINVAL, "autotune needs a non-empty sample");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int old = t->batch_nodes_per_thread;
+    int best_npt = 0;
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    rc = bpq::cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
+    if (rc) return rc;
+    rc = bpq::cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
+    if (rc) {
+        cudaEventDestroy(e0);
+        return rc;
+    }
+    const bpq_batch_item item{t, syn_dev, prior_dev, B, est_dev, conv_dev, iters_dev};
+    for (int npt = 1; npt <= 2 && !rc; ++npt) {
+        t->batch_nodes_per_thread = npt;
+        bpq::LaunchShape shape;
+        if (bpq::decode_batch_shape(t, variant, &shape)) continue;
+        bpq_batch *plan = nullptr;
+        rc = bpq_batch_plan(&item, 1, variant, params, max_iter, work_dev, work_bytes, stream, &plan);
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {  // one warm-up, two timed
+            if (rep == 1) rc = bpq::cuda_check(cudaEventRecord(e0, st), "cudaEventRecord");
+            if (!rc) rc = bpq_batch_launch(plan, stream);
+        }
+        if (!rc) rc = bpq::cuda_check(cudaEventRecord(e1, st), "cudaEventRecord");
+        if (!rc) rc = bpq::cuda_check(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        if (!rc) rc = bpq::cuda_check(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        bpq_batch_free(plan);
+        if (!rc && ms / 2 < best) {
+            best = ms / 2;
+            best_npt = npt;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc || best_npt == 0) {
+        t->batch_nodes_per_thread = old;
+        return rc ? rc : fail(BPQ_EINVAL, "no batched shape fits this code");
+    }
+    t->batch_nodes_per_thread = best_npt;
+    if (nodes_per_thread) *nodes_per_thread = best_npt;
+    if (best_ms) *best_ms = best;
+    return BPQ_OK;
+}
 
 }  // extern "C"

@@ -84,6 +84,8 @@ struct bpq_tanner {
     // launch preferences (0 = automatic); with two shots per thread the
     // first two describe a shot group (which decodes two shots at a time)
     int threads_per_shot = 0, shots_per_cta = 0, shots_per_thread = 0;
+    // nodes per thread inside the batched kernel and the servers (0 = automatic)
+    int batch_nodes_per_thread = 0;
     // run the bounds-checked kernels (bpq_set_debug_checks)
     bool debug_checks = false;
 };

@@ -107,28 +107,49 @@ int decode_launch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
     return BPQ_OK;
 }
 
-int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
-    // the code's own shape if it has at most two nodes per thread, else two
-    // nodes per thread; as many shot groups as fit in kBatchThreads
-    LaunchShape own;
+namespace {
+// Shape of a code in the batched kernel with npt (1 or 2) nodes per thread:
+// the fewest threads per shot group that cover max(N, M), and as many shot
+// groups as fit in kBatchThreads threads and 227 KB of shared memory.
+int batch_shape_npt(const bpq_tanner *t, int variant, int npt, LaunchShape *s) {
     const int nodes = t->N > t->M ? t->N : t->M;
-    int T = 0;
-    if (decode_launch_shape(t, variant, &own) == BPQ_OK && own.npt <= 2) T = own.T;
-    if (T == 0) T = (((nodes + 1) / 2 + 31) / 32) * 32;
+    const int T = (((nodes + npt - 1) / npt + 31) / 32) * 32;
     if (T > kBatchThreads) return fail(BPQ_EINVAL, "code too large for the batched kernel");
     const int max_groups = T == 32 ? kMaxGroupsPerCta : 15;
     int gpc = kBatchThreads / T;
     if (gpc > max_groups) gpc = max_groups;
     s->T = T;
     s->G = T / 32;
-    s->npt = (nodes + T - 1) / T;
-    s->groups_per_cta = gpc;
+    s->npt = npt;
     s->n_pad = (t->N + 3) & ~3;
     s->slots_floats = (uint32_t)(4 * s->n_pad + 4);
     const int nstate = state_arrays(variant);
     s->group_bytes = (uint32_t)(4 * s->slots_floats + 4 * nstate * s->n_pad);
-    s->smem = kSmemHeader + kDescBytes + t->table.size() + (size_t)12 * s->n_pad + (size_t)gpc * s->group_bytes;
+    const size_t fixed = kSmemHeader + kDescBytes + t->table.size() + (size_t)12 * s->n_pad;
+    while (gpc > 1 && fixed + (size_t)gpc * s->group_bytes > 227 * 1024) --gpc;
+    s->groups_per_cta = gpc;
+    s->smem = fixed + (size_t)gpc * s->group_bytes;
     if (s->smem > 227 * 1024) return fail(BPQ_EINVAL, "a code of the batch needs more than 227 KB of shared memory");
+    return BPQ_OK;
+}
+}  // namespace
+
+int decode_batch_shape(const bpq_tanner *t, int variant, LaunchShape *s) {
+    if (t->batch_nodes_per_thread > 0) return batch_shape_npt(t, variant, t->batch_nodes_per_thread, s);
+    // automatic: the node count per thread that keeps the most node slots of
+    // a CTA busy (groups x nodes / (npt x kBatchThreads)); on a tie two nodes
+    // per thread, whose twice as many groups balance the item's shots better
+    LaunchShape one, two;
+    const std::string keep = bpq_last_error();
+    const int rc1 = batch_shape_npt(t, variant, 1, &one);
+    const int rc2 = batch_shape_npt(t, variant, 2, &two);
+    if (rc2) {
+        if (rc1) return rc2;
+        *s = one;
+    } else {
+        *s = !rc1 && 2 * one.groups_per_cta > two.groups_per_cta ? one : two;
+    }
+    set_error(keep);
     return BPQ_OK;
 }
 

@@ -825,15 +825,42 @@ __global__ void __launch_bounds__(NPT <= 2 ? 1024 : 512, 1) decode_kernel(const 
     }
 }
 
+// The shots of the current item taken by one shot group of the batched
+// kernel: the group takes the item's shots one by one from the item's
+// counter until none are left.  NPT, SPLIT and FULL are the item's nodes
+// per thread and table layout, so each item runs the decode_shot
+// specialisation that the one-code kernel runs for it.
+template <int VARIANT, int NPT, bool SPLIT, bool FULL>
+__device__ __forceinline__ void batch_item_shots(const DecodeArgs &a, const ThreadAdj<2> &adj2, const GroupMem &m,
+                                                 uint32_t *next, int *slot, int T, int tg, int G, int bar_id) {
+    ThreadAdj<NPT> adj;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        adj.cs_lo[k] = adj2.cs_lo[k];
+        adj.cs_hi[k] = adj2.cs_hi[k];
+        adj.info[k] = adj2.info[k];
+        adj.pp[k] = adj2.pp[k];
+    }
+    for (;;) {
+        if (tg == 0) *slot = (int)atomicAdd(next, 1u);
+        group_sync(G, bar_id);
+        const int shot = *slot;
+        if (shot >= a.B) break;
+        decode_shot<VARIANT, NPT, false, SPLIT, FULL>(a, adj, m, NPT, T, tg, G, bar_id, shot, a.alpha);
+    }
+}
+
 // Many codes in one launch.  A CTA of kBatchThreads works on one item (a
 // code's batch) at a time: it splits into that code's shot groups (T_g
-// threads each), which take the item's shots one by one from the item's
-// global counter until none are left; only then does the CTA synchronise,
-// pick the next item with shots left (scanning from its starting item) and
-// re-stage that code's adjacency (bulk TMA) and prior.  Every shot is
-// decoded by decode_shot, so results equal those of decode_kernel bit for
-// bit.
-template <int VARIANT, int NPT>
+// threads each, one or two nodes per thread), which take the item's shots
+// until none are left; only then does the CTA synchronise, pick the next
+// item with shots left (scanning from its starting item) and re-stage that
+// code's adjacency (bulk TMA) and prior.  Every shot is decoded by the
+// decode_shot specialisation of decode_kernel for its code (nodes per
+// thread and layout), so results equal those of decode_kernel bit for bit.
+// GENERIC: items may use the generic table layout; without it every item
+// has the split layout, and the kernel holds only the split paths.
+template <int VARIANT, bool GENERIC>
 __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const BatchArgs b) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
@@ -851,7 +878,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
     int cur = -1;
     int from = b.start[blockIdx.x < (unsigned)kMaxBatchCtas ? blockIdx.x : 0];
     uint32_t phase = 0;
-    ThreadAdj<NPT> adj;
+    ThreadAdj<2> adj;
     for (;;) {
         if (tid == 0) {
             int pick = -1;
@@ -867,11 +894,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
         if (g < 0) break;
         from = g;
         if (g != cur) {
-            // switch code: descriptor, adjacency (bulk TMA), prior, zero slots.
-            // The new table may cover the previous item's prior, message slots
-            // and state, written with ordinary stores: every thread fences
-            // them against the async proxy before the barrier that precedes
-            // the copy.
+            // switch item: descriptor, adjacency (bulk TMA), prior, zero
+            // slots.  The new table may cover the previous item's prior,
+            // message slots and state, written with ordinary stores: every
+            // thread fences them against the async proxy before the barrier
+            // that precedes the copy.
             const uint32_t *src = reinterpret_cast<const uint32_t *>(b.codes + g);
             for (int w = tid; w < (int)(sizeof(DecodeArgs) / 4); w += blockDim.x)
                 reinterpret_cast<uint32_t *>(desc)[w] = src[w];
@@ -895,7 +922,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
                 const GroupMem m = group_mem(*desc, tab, group);
                 m.slots[4 * desc->n_pad] = 0.f;
             }
-            load_adjacency<NPT>(*desc, tab, T, tid - group * T, desc->npt, adj);
+            load_adjacency<2>(*desc, tab, T, tid - group * T, desc->npt, adj);
             __syncthreads();
             cur = g;
         }
@@ -905,19 +932,24 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
         if (group < a.groups_per_cta) {
             const GroupMem m = group_mem(a, tab, group);
             const int bar_id = 1 + group;
-            for (;;) {
-                if (tg == 0) grp_shot[group] = (int)atomicAdd(b.work + 2 + g, 1u);
-                group_sync(G, bar_id);
-                const int shot = grp_shot[group];
-                if (shot >= a.B) break;
-                // (codes without padding run the padded split-layout code
-                // here, with the same results: a third inlined copy would add
-                // code to a kernel already at its 64-register cap)
-                if (a.split)
-                    decode_shot<VARIANT, NPT, false, true, false>(a, adj, m, a.npt, T, tg, G, bar_id, shot, a.alpha);
+            uint32_t *next = b.work + 2 + g;
+            int *slot = grp_shot + group;
+            const bool one = a.npt == 1;
+            if (a.split == 2) {
+                if (one)
+                    batch_item_shots<VARIANT, 1, true, true>(a, adj, m, next, slot, T, tg, G, bar_id);
                 else
-                    decode_shot<VARIANT, NPT, false, false, false>(a, adj, m, a.npt, T, tg, G, bar_id, shot,
-                                                                   a.alpha);
+                    batch_item_shots<VARIANT, 2, true, true>(a, adj, m, next, slot, T, tg, G, bar_id);
+            } else if (a.split == 1 || !GENERIC) {
+                if (one)
+                    batch_item_shots<VARIANT, 1, true, false>(a, adj, m, next, slot, T, tg, G, bar_id);
+                else
+                    batch_item_shots<VARIANT, 2, true, false>(a, adj, m, next, slot, T, tg, G, bar_id);
+            } else if (GENERIC) {
+                if (one)
+                    batch_item_shots<VARIANT, 1, false, false>(a, adj, m, next, slot, T, tg, G, bar_id);
+                else
+                    batch_item_shots<VARIANT, 2, false, false>(a, adj, m, next, slot, T, tg, G, bar_id);
             }
         }
         __syncthreads();
@@ -960,9 +992,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_batch_kernel(const Ba
             case 9: return BPQ_PICK_NPT(V, 4, true);                                     \
         }                                                                                \
         return nullptr;                                                                  \
-    }                                                                                    \
-    BatchKernelFn NAME##_batch(int npt) {                                                \
-        return npt <= 2 ? dk::decode_batch_kernel<V, 2> : nullptr;                       \
+    }
+
+// The batched kernel of one variant (instantiated in a translation unit of
+// its own): generic = items may use the generic table layout.
+#define BPQ_DEFINE_PICK_BATCH(NAME, V)                                                   \
+    BatchKernelFn NAME(bool generic) {                                                   \
+        return generic ? dk::decode_batch_kernel<V, true> : dk::decode_batch_kernel<V, false>; \
     }
 
 // The non-trace kernels of one variant for split tables without padding

@@ -76,18 +76,20 @@ using BatchKernelFn = void (*)(const BatchArgs);
 // non-trace kernels for split tables without padding.
 DecodeKernelFn pick_plain(int npt, bool trace, bool split);
 DecodeKernelFn pick_plain_full(int npt);
-BatchKernelFn pick_plain_batch(int npt);
 DecodeKernelFn pick_momentum(int npt, bool trace, bool split);
 DecodeKernelFn pick_momentum_full(int npt);
-BatchKernelFn pick_momentum_batch(int npt);
 DecodeKernelFn pick_adagrad(int npt, bool trace, bool split);
 DecodeKernelFn pick_adagrad_full(int npt);
-BatchKernelFn pick_adagrad_batch(int npt);
 DecodeKernelFn pick_ewainit(int npt, bool trace, bool split);
 DecodeKernelFn pick_ewainit_full(int npt);
 DecodeKernelFn pick_aewa(int npt, bool trace, bool split);
 DecodeKernelFn pick_aewa_full(int npt);
-BatchKernelFn pick_ewainit_batch(int npt);
+// Batched kernels (decode_*_batch.cu): generic = some item uses the generic
+// table layout (else every item has the split layout).
+BatchKernelFn pick_plain_batch(bool generic);
+BatchKernelFn pick_momentum_batch(bool generic);
+BatchKernelFn pick_adagrad_batch(bool generic);
+BatchKernelFn pick_ewainit_batch(bool generic);
 // Two shots per thread (decode_pair.cuh), split tables, npt in {1, 2}; the
 // _full functions for split tables without padding.
 DecodeKernelFn pick_plain_pair(int npt);

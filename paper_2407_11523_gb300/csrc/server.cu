@@ -39,7 +39,7 @@
 using bpq::fail;
 
 namespace bpq {
-BatchKernelFn pick_batch_kernel(int variant, int npt);
+BatchKernelFn pick_batch_kernel(int variant, bool generic);
 }
 
 namespace {
@@ -335,6 +335,7 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
     s->max_batch = max_batch;
     int rc = BPQ_OK;
     int npt_max = 1;
+    bool generic = false;  // some code uses the generic table layout
     for (int c = 0; c < n_codes && !rc; ++c) {
         const bpq_tanner *t = codes[c];
         if (!t || !t->dev_blob || t->device != device) {
@@ -360,6 +361,7 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
         a.npt = sh.npt;
         a.groups_per_cta = gpc;
         npt_max = std::max(npt_max, sh.npt);
+        generic = generic || a.split == 0;
         s->smem = std::max(s->smem, sh.smem);
         s->codes.push_back(t);
         s->tmpl.push_back(a);
@@ -369,7 +371,7 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
     if (!rc && s->smem > 227 * 1024) rc = fail(BPQ_EINVAL, "a code needs more than 227 KB of shared memory");
     if (!rc) rc = bpq::cuda_set_device(device);
     if (!rc) {
-        s->fn = bpq::pick_batch_kernel(variant, npt_max);
+        s->fn = bpq::pick_batch_kernel(variant, generic);
         if (!s->fn) {
             free_server(s);
             return fail(BPQ_EINVAL, "no batched kernel for these codes");

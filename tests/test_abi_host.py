@@ -189,3 +189,30 @@ def test_message_layout_of_each_code_family(bpq):
     T = np.zeros((3, 1), dtype=np.uint8)
     T[:, 0] = 1  # one qubit on three X checks
     assert bpq.Tanner(H=T).layout() == 0
+
+
+def test_batch_shapes(bpq):
+    """Shot groups of a code inside the batched kernel: the fewest threads per
+    group for the chosen nodes per thread, as many groups as fit in 1024
+    threads (15 multi-warp, 32 one-warp at most); automatic = the choice with
+    more busy node slots per CTA, two nodes per thread on a tie; independent
+    of the one-code launch shape."""
+    assert bpq.Tanner("planar", 17).batch_launch() == (288, 3, 2)   # 3 x 545 / 2048 > 1 x 545 / 1024
+    assert bpq.Tanner("planar", 9).batch_launch() == (160, 6, 1)    # 6 x 145 / 1024 > 10 x 145 / 2048
+    assert bpq.Tanner("toric", 8).batch_launch() == (128, 8, 1)
+    assert bpq.Tanner("toric", 16).batch_launch() == (256, 4, 2)    # tie: 2 x 512 / 1024 = 4 x 512 / 2048
+    assert bpq.Tanner("planar", 5).batch_launch() == (32, 32, 2)    # one-warp groups
+    assert bpq.Tanner("planar", 25).batch_launch() == (608, 1, 2)   # 1201 nodes: no one-node shape
+    t = bpq.Tanner("planar", 17)
+    t.set_launch(160, 1)   # four nodes per thread in bpq_decode
+    assert t.batch_launch() == (288, 3, 2)
+    t.set_batch_launch(1)
+    assert t.batch_launch() == (576, 1, 1)
+    t.set_batch_launch(0)
+    assert t.batch_launch() == (288, 3, 2)
+    with pytest.raises(bpq.BPQError):
+        t.set_batch_launch(3)
+    with pytest.raises(bpq.BPQError):
+        bpq.Tanner("planar", 25).set_batch_launch(1)    # 1201 threads per group
+    with pytest.raises(bpq.BPQError):
+        t.batch_launch("aewa")

@@ -44,7 +44,42 @@ def test_batched_equals_per_code_decode(bpq, variant):
         for a, b in zip(got, ref):
             assert torch.equal(a, b), (t.N, variant)
     info = plan.info()
-    assert info["shots"] == sum(sizes) and info["npt_max"] >= 2
+    assert info["shots"] == sum(sizes) and info["npt_max"] == max(t.batch_launch(variant)[2] for t, _, _ in items)
+
+
+@pytest.mark.parametrize("variant", ["ewainit", "plain", "momentum", "adagrad"])
+@pytest.mark.parametrize("npt", [1, 2])
+def test_batched_shapes_equal_per_code_decode(bpq, variant, npt):
+    """Every code of the mix with one and with two nodes per thread inside
+    the batched kernel (different shot groups per CTA, and the one-node and
+    the padding-free specialisations): results unchanged bit for bit."""
+    sizes = [700, 500, 600, 300, 257, 400, 300, 31]
+    items = build_items(bpq, sizes, seed=11)
+    for t, _, _ in items:
+        if npt == 1 and max(t.N, t.M) > 1024:
+            continue   # planar d = 25: one node per thread does not fit
+        t.set_batch_launch(npt)
+        assert t.batch_launch(variant)[2] == npt
+    outs = bpq.BatchPlan(items, variant=variant, max_iter=100).run()
+    for (t, syn, prior), got in zip(items, outs):
+        ref = bpq.decode(t, syn, prior, variant, max_iter=100)
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b), (t.N, variant, npt)
+
+
+def test_batch_autotune_keeps_results(bpq):
+    """The batched autotuner stores one of the two shapes; a plan built after
+    it gives the one-code decoder's results."""
+    items = build_items(bpq, [2000, 1500, 1800, 900, 300, 700, 800, 100], seed=21)
+    for t, syn, prior in items:
+        npt, ms = bpq.autotune_batch(t, syn, prior, "ewainit", max_iter=100)
+        assert npt in (1, 2) and ms > 0
+        assert t.batch_launch("ewainit")[2] == npt
+    outs = bpq.BatchPlan(items, variant="ewainit", max_iter=100).run()
+    for (t, syn, prior), got in zip(items, outs):
+        ref = bpq.decode(t, syn, prior, "ewainit", max_iter=100)
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b), t.N
 
 
 def test_batched_launch_in_cuda_graph(bpq):
@@ -113,9 +148,11 @@ def y_rotated(H, qubits):
 
 
 @pytest.mark.parametrize("variant", ["ewainit", "adagrad"])
-def test_batched_mixed_layouts(bpq, variant):
+@pytest.mark.parametrize("npt", [0, 1, 2])
+def test_batched_mixed_layouts(bpq, variant, npt):
     """Codes in the generic layout (Y entries) and in the split layout share
-    one batched launch; each result equals the one-code decoder's."""
+    one batched launch, with each shape choice; each result equals the
+    one-code decoder's."""
     from inputs import random_tree_code
     rng = np.random.default_rng(5)
     H7 = bpq.Tanner("planar", 7).dense()
@@ -124,6 +161,7 @@ def test_batched_mixed_layouts(bpq, variant):
     ch = oracle.depolarizing(0.06)
     items = []
     for k, t in enumerate(codes):
+        t.set_batch_launch(npt)
         _, syn = bpq.sample(t, *ch, seed=400 + k, shot0=0, B=700 + 37 * k)
         items.append((t, syn, bpq.prior_tensor(t, *ch)))
     plan = bpq.BatchPlan(items, variant=variant, max_iter=60)
