@@ -291,10 +291,23 @@ int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
  * variant: plain, Momentum, AdaGrad or EWAInit BP (EINVAL otherwise).
  * Arguments, layouts, ownership, asynchrony and errors as bpq_decode; iters
  * counts sweeps.  EINVAL also when one shot's state does not fit in shared
- * memory (about 4600 edges for EWAInit-BP). */
+ * memory (about 10^4 edges for EWAInit-BP).  A warp decodes one shot, or two
+ * (bpq_set_serial_shots_per_warp) with the same per-shot results bit for
+ * bit. */
 int bpq_decode_serial(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
                       const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
                       uint8_t *iters_dev, void *work_dev, void *stream);
+
+/* Shots per warp of bpq_decode_serial (an implementation choice; the paper
+ * has no GPU design): 1 = each warp decodes one shot; 2 = each warp decodes
+ * two, its lanes working on the same qubit of both, whose messages share
+ * 64-bit shared-memory slots and packed f32x2 arithmetic (each shot stops on
+ * its own and the warp takes the next one for that half); 0 = automatic (2
+ * once the batch holds at least 4 shots per resident one-shot warp, e.g.
+ * 9120 toric d = 15 shots on a GB300).  The trace keeps one shot per warp.
+ * Errors: EINVAL (a value outside 0..2); bpq_decode_serial returns EINVAL
+ * for 2 when two shots of the code do not fit in shared memory. */
+int bpq_set_serial_shots_per_warp(bpq_tanner *t, int shots_per_warp);
 
 /* Per-sweep record of the serial schedule, in bpq_decode_trace's layout:
  * exactly T sweeps, no stopping rule; m_v2c_dev [B][T+1][E] holds each

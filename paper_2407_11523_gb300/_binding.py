@@ -77,6 +77,7 @@ def lib():
                                        ctypes.POINTER(ctypes.c_float)]),
             "bpq_set_shots_per_thread": (i, [P, i]),
             "bpq_set_debug_checks": (i, [P, i]),
+            "bpq_set_serial_shots_per_warp": (i, [P, i]),
             "bpq_get_shots_per_thread": (i, [P, i, pi]),
             "bpq_check_logical": (i, [P, P, P, i, P, P]),
             "bpq_probe_peak": (i, [i, i, i, i, P, P]),
@@ -241,6 +242,11 @@ class Tanner:
         """1: one shot per thread; 2: two shots per thread (split tables);
         0: automatic (bpq_set_shots_per_thread)."""
         _check(lib().bpq_set_shots_per_thread(self._h, k), "bpq_set_shots_per_thread")
+
+    def set_serial_shots_per_warp(self, k=0):
+        """Shots per warp of the serial-schedule kernel: 1, 2, or 0 =
+        automatic (bpq_set_serial_shots_per_warp)."""
+        _check(lib().bpq_set_serial_shots_per_warp(self._h, k), "bpq_set_serial_shots_per_warp")
 
     def set_debug_checks(self, on=True):
         """Run the bounds-checked decode kernels (bpq_set_debug_checks)."""

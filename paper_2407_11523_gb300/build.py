@@ -20,7 +20,7 @@ SOURCES = ["api.cu", "batch.cu", "server.cu", "train.cu", "decode.cu", "decode_p
            "decode_adagrad_full.cu", "decode_ewainit_full.cu", "decode_aewa_full.cu", "decode_plain_pair.cu",
            "decode_momentum_pair.cu", "decode_adagrad_pair.cu", "decode_ewainit_pair.cu", "decode_plain_batch.cu",
            "decode_momentum_batch.cu", "decode_adagrad_batch.cu", "decode_ewainit_batch.cu", "serve_kernels.cu",
-           "decode_debug.cu", "serial.cu", "tanner.cpp"]
+           "decode_debug.cu", "serial.cu", "serial_pair.cu", "tanner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

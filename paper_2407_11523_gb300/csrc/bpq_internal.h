@@ -22,15 +22,21 @@ void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 
 // One qubit of the serial schedule's sweep (48 bytes, 16-byte aligned); the
-// serial table lists them level by level (see serial.cu).
+// serial table lists them level by level (see serial.cu).  Message slots
+// index the kernel's per-shot message array: every edge has one slot, laid
+// out so that the lanes of one access fall in distinct shared-memory banks;
+// two extra slots follow the edges' (zero: reads as a certain message with
+// positive sign, the identity of the check rule; trash: takes writes of
+// padding edges).
 struct SerialVar {
+    uint16_t own[4];     // slot of the qubit's edge k (the trash slot for padding)
+    uint16_t oth[4][3];  // slots of the other edges of edge k's check (the zero slot for padding)
+    uint16_t chk[4];     // the check of edge k (0 for padding)
     uint16_t j;          // the qubit
-    uint8_t deg;         // its number of edges (<= 4)
-    uint8_t pauli;       // H_ij of edge k in bits 2k, 2k+1 (0 for k >= deg)
-    uint16_t own[4];     // check-major index of edge k (E, the zero slot, for k >= deg)
-    uint16_t chk[4];     // the check of edge k
-    uint16_t oth[4][3];  // the other edges of that check (E for padding)
-    uint16_t pad[2];
+    uint8_t pauli;       // H_ij of edge k in bits 2k, 2k+1 (0 for padding)
+    uint8_t last;        // bit k: the qubit is the last of edge k's check in the sweep
+    uint8_t real;        // bit k: edge k exists (not padding)
+    uint8_t pad[3];
 };
 static_assert(sizeof(SerialVar) == 48, "SerialVar layout");
 
@@ -64,10 +70,14 @@ struct bpq_tanner {
     std::vector<uint8_t> table_split;
     std::vector<int32_t> var_canon_split;  // 4 n4, indexed by split slot
     // Serial schedule (bpq::build_serial_table): SerialVar[N] in level order |
-    // level_ptr u16[levels + 1] | chk_ptr u16[M + 1], padded to 16 bytes.
+    // level_ptr u16[levels + 1] | canon u16[N][4] (check-major index of each
+    // qubit's edge k, E for padding; 16-byte aligned, read by the trace
+    // kernels only, so the kernels stage the table up to it), padded to 16
+    // bytes; serial_slots
+    // message slots for the edges, then the zero and the trash slot.
     std::vector<uint8_t> serial;
-    int serial_levels = 0;
-    uint32_t serial_off_levels = 0, serial_off_chkptr = 0;
+    int serial_levels = 0, serial_slots = 0;
+    uint32_t serial_off_levels = 0, serial_off_canon = 0;
 
     // device
     int device = -1;
@@ -86,6 +96,8 @@ struct bpq_tanner {
     int threads_per_shot = 0, shots_per_cta = 0, shots_per_thread = 0;
     // nodes per thread inside the batched kernel and the servers (0 = automatic)
     int batch_nodes_per_thread = 0;
+    // shots per warp of the serial-schedule kernel (0 = automatic)
+    int serial_shots_per_warp = 0;
     // run the bounds-checked kernels (bpq_set_debug_checks)
     bool debug_checks = false;
 };

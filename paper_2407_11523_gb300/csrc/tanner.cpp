@@ -13,6 +13,7 @@
 // plane).  Qubit order: block 1 row-major, then block 2 row-major; check
 // order: X-type rows, then Z-type rows.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <new>
 
@@ -153,9 +154,66 @@ int build_tables(bpq_tanner *t) {
     return build_serial_table(t);
 }
 
+namespace {
+// Message slots of the serial kernel's edges: slot = bank + 32 * row, with
+// bank chosen greedily so that the edges one warp instruction touches (the
+// k-th edge, or its check's r-th other edge, of the qubits of one 32-lane
+// step of a level) fall in distinct banks where possible.  Edges are
+// coloured in sweep order; each bank holds at most ceil(E / 32) + 1 edges.
+std::vector<int> colour_serial_slots(const std::vector<std::array<int, 4>> &at, const std::vector<int> &edge_chk,
+                                     const std::vector<int32_t> &chk_ptr, const std::vector<int> &order,
+                                     const std::vector<int> &lp, int E, int *nslots) {
+    const int nlev = (int)lp.size() - 1;
+    std::vector<std::vector<int>> groups;
+    for (int l = 0; l < nlev; ++l)
+        for (int s0 = lp[l]; s0 < lp[l + 1]; s0 += 32) {
+            const int s1 = std::min(lp[l + 1], s0 + 32);
+            for (int k = 0; k < 4; ++k)
+                for (int r = 0; r < 4; ++r) {
+                    std::vector<int> g;
+                    for (int v = s0; v < s1; ++v) {
+                        const int e = at[order[v]][k];
+                        if (e < 0) continue;
+                        const int i = edge_chk[e];
+                        if (r == 3) {
+                            g.push_back(e);
+                            continue;
+                        }
+                        int f = 0;
+                        for (int x = chk_ptr[i]; x < chk_ptr[i + 1]; ++x)
+                            if (x != e && f++ == r) g.push_back(x);
+                    }
+                    if (!g.empty()) groups.push_back(std::move(g));
+                }
+        }
+    std::vector<std::vector<int>> edge_groups(E);
+    for (int gi = 0; gi < (int)groups.size(); ++gi)
+        for (int e : groups[gi]) edge_groups[e].push_back(gi);
+    const int cap = (E + 31) / 32 + 1;
+    std::vector<int> bank(E, -1), fill(32, 0), slot(E);
+    for (int v = 0; v < (int)order.size(); ++v)
+        for (int e : at[order[v]]) {
+            if (e < 0) continue;
+            int cost[32] = {0};
+            for (int gi : edge_groups[e])
+                for (int x : groups[gi])
+                    if (bank[x] >= 0) ++cost[bank[x]];
+            int best = -1;
+            for (int b = 0; b < 32; ++b)
+                if (fill[b] < cap && (best < 0 || cost[b] < cost[best] || (cost[b] == cost[best] && fill[b] < fill[best])))
+                    best = b;
+            bank[e] = best;
+            slot[e] = best + 32 * fill[best]++;
+        }
+    int top = 0;
+    for (int b = 0; b < 32; ++b) top = std::max(top, fill[b]);
+    *nslots = 32 * top;
+    return slot;
+}
+}  // namespace
+
 int build_serial_table(bpq_tanner *t) {
     const int N = t->N, M = t->M, E = t->E;
-    if (E >= 0xFFFF || M >= 0xFFFF) return fail(BPQ_EINVAL, "code too large for the serial table");
     // level(j) = 1 + the largest level among the earlier qubits sharing a check with j
     std::vector<std::vector<int>> var_edges(N);
     std::vector<int> edge_chk(E);
@@ -164,56 +222,85 @@ int build_serial_table(bpq_tanner *t) {
             var_edges[t->chk_var[e]].push_back(e);
             edge_chk[e] = i;
         }
-    std::vector<int> level(N), chk_last(M, -1);
+    std::vector<int> level(N), chk_last(M, -1), chk_lastq(M, -1);
     int nlevels = 0;
     for (int j = 0; j < N; ++j) {
         int l = 0;
         for (int e : var_edges[j]) l = std::max(l, chk_last[edge_chk[e]] + 1);
         level[j] = l;
-        for (int e : var_edges[j]) chk_last[edge_chk[e]] = l;
+        for (int e : var_edges[j]) {
+            chk_last[edge_chk[e]] = l;
+            chk_lastq[edge_chk[e]] = j;  // qubits in index order: the last one stays
+        }
         nlevels = std::max(nlevels, l + 1);
     }
     std::vector<int> order(N);
     for (int j = 0; j < N; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return level[x] < level[y]; });
+    std::vector<int> lp(nlevels + 1);
+    for (int l = 0, v = 0; l <= nlevels; ++l) {
+        while (v < N && level[order[v]] < l) ++v;
+        lp[l] = v;
+    }
+    // edge at each of a qubit's four positions (-1: padding): in increasing
+    // check order, or (split layout) the X edges at 0, 1 and the Z edges at
+    // 2, 3
+    std::vector<std::array<int, 4>> at(N);
+    for (int j = 0; j < N; ++j) {
+        at[j] = {-1, -1, -1, -1};
+        int nx = 0, nz = 0;
+        for (int q = 0; q < (int)var_edges[j].size(); ++q) {
+            const int e = var_edges[j][q];
+            at[j][!t->split ? q : t->chk_pauli[e] == 1 ? nx++ : 2 + nz++] = e;
+        }
+    }
+    int nslots = 0;
+    const std::vector<int> slot = colour_serial_slots(at, edge_chk, t->chk_ptr, order, lp, E, &nslots);
+    if (nslots + 2 > 0xFFFF || M >= 0xFFFF || E >= 0xFFFF || N > 0xFFFF)
+        return fail(BPQ_EINVAL, "code too large for the serial table");
+    const uint16_t kZero = (uint16_t)nslots, kTrash = (uint16_t)(nslots + 1);
 
     const size_t vars_bytes = sizeof(SerialVar) * (size_t)N;
     const size_t off_levels = vars_bytes;
-    const size_t off_chkptr = off_levels + 2 * (size_t)(nlevels + 1);
-    const size_t bytes = (off_chkptr + 2 * (size_t)(M + 1) + 15) & ~size_t(15);
+    const size_t off_canon = (off_levels + 2 * (size_t)(nlevels + 1) + 15) & ~size_t(15);
+    const size_t bytes = (off_canon + 8 * (size_t)N + 15) & ~size_t(15);
     t->serial.assign(bytes, 0);
     SerialVar *vars = reinterpret_cast<SerialVar *>(t->serial.data());
-    uint16_t *lp = reinterpret_cast<uint16_t *>(t->serial.data() + off_levels);
-    uint16_t *cp = reinterpret_cast<uint16_t *>(t->serial.data() + off_chkptr);
+    uint16_t *lpt = reinterpret_cast<uint16_t *>(t->serial.data() + off_levels);
+    uint16_t *canon = reinterpret_cast<uint16_t *>(t->serial.data() + off_canon);
     for (int v = 0; v < N; ++v) {
         const int j = order[v];
         SerialVar &sv = vars[v];
         sv.j = (uint16_t)j;
-        sv.deg = (uint8_t)var_edges[j].size();
         sv.pauli = 0;
+        sv.last = 0;
+        sv.real = 0;
         for (int k = 0; k < 4; ++k) {
-            sv.own[k] = (uint16_t)E;
+            sv.own[k] = kTrash;
             sv.chk[k] = 0;
-            for (int f = 0; f < 3; ++f) sv.oth[k][f] = (uint16_t)E;
+            canon[4 * v + k] = (uint16_t)E;
+            for (int f = 0; f < 3; ++f) sv.oth[k][f] = kZero;
         }
-        for (int k = 0; k < sv.deg; ++k) {
-            const int e = var_edges[j][k], i = edge_chk[e];
-            sv.own[k] = (uint16_t)e;
+        for (int k = 0; k < 4; ++k) {
+            const int e = at[j][k];
+            if (e < 0) continue;
+            const int i = edge_chk[e];
+            sv.real |= (uint8_t)(1u << k);
+            sv.own[k] = (uint16_t)slot[e];
             sv.chk[k] = (uint16_t)i;
+            canon[4 * v + k] = (uint16_t)e;
             sv.pauli |= (uint8_t)(t->chk_pauli[e] << (2 * k));
+            if (chk_lastq[i] == j) sv.last |= (uint8_t)(1u << k);
             int f = 0;
             for (int x = t->chk_ptr[i]; x < t->chk_ptr[i + 1]; ++x)
-                if (x != e) sv.oth[k][f++] = (uint16_t)x;
+                if (x != e) sv.oth[k][f++] = (uint16_t)slot[x];
         }
     }
-    for (int l = 0, v = 0; l <= nlevels; ++l) {
-        while (v < N && level[order[v]] < l) ++v;
-        lp[l] = (uint16_t)v;
-    }
-    for (int i = 0; i <= M; ++i) cp[i] = (uint16_t)t->chk_ptr[i];
+    for (int l = 0; l <= nlevels; ++l) lpt[l] = (uint16_t)lp[l];
     t->serial_levels = nlevels;
+    t->serial_slots = nslots;
     t->serial_off_levels = (uint32_t)off_levels;
-    t->serial_off_chkptr = (uint32_t)off_chkptr;
+    t->serial_off_canon = (uint32_t)off_canon;
     return BPQ_OK;
 }
 

@@ -216,3 +216,12 @@ def test_batch_shapes(bpq):
         bpq.Tanner("planar", 25).set_batch_launch(1)    # 1201 threads per group
     with pytest.raises(bpq.BPQError):
         t.batch_launch("aewa")
+
+
+def test_serial_shots_per_warp_refusals(bpq):
+    t = bpq.Tanner("planar", 5)
+    for k in (0, 1, 2):
+        t.set_serial_shots_per_warp(k)
+    for k in (3, -1):
+        with pytest.raises(bpq.BPQError):
+            t.set_serial_shots_per_warp(k)

@@ -95,9 +95,12 @@ def test_serial_messages_trees_and_trapping_set(bpq, variant):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_serial_decode_planar_d5_10k_shots(bpq, variant):
-    """Config C1 under the serial schedule: decisions, flags, LER."""
+@pytest.mark.parametrize("spw", [1, 2])
+def test_serial_decode_planar_d5_10k_shots(bpq, variant, spw):
+    """Config C1 under the serial schedule, one and two shots per warp:
+    decisions, flags, LER."""
     t = bpq.Tanner("planar", 5)
+    t.set_serial_shots_per_warp(spw)
     H = t.dense()
     ch = oracle.depolarizing(0.05)
     B = 10000
@@ -159,3 +162,37 @@ def test_serial_partition_invariance_and_refusals(bpq):
         bpq.decode(t, syn, prior, "aewa", max_iter=60, schedule="serial")
     empty = bpq.decode(t, syn[:0].contiguous(), prior, "ewainit", max_iter=60, schedule="serial")
     assert empty[0].shape == (0, t.N)
+
+
+def serial_codes(bpq):
+    """Split-layout codes (planar, toric without padding, XZZX) and codes in
+    the generic layout (a tree code, a trapping set, a planar code with Y
+    entries)."""
+    from test_gpu_batch import y_rotated
+    H7 = bpq.Tanner("planar", 7).dense()
+    rng = np.random.default_rng(9)
+    return [bpq.Tanner("planar", 5), bpq.Tanner("toric", 8), bpq.Tanner("xzzx", 7), bpq.Tanner("planar", 13),
+            bpq.Tanner(H=random_tree_code(8, seed=5)), bpq.Tanner(H=trapping_set_code()),
+            bpq.Tanner(H=y_rotated(H7, rng.choice(H7.shape[1], 30, replace=False)))]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_serial_two_shots_per_warp_equal_one(bpq, variant):
+    """Two shots per warp give the one-shot kernel's results bit for bit
+    (every step rounds alike), on split and generic layouts, with a ragged
+    batch, max_iter 1 and 60, and a single shot (one half of the warp
+    idle)."""
+    ch = oracle.depolarizing(0.07)
+    for k, t in enumerate(serial_codes(bpq)):
+        _, syn = bpq.sample(t, *ch, seed=700 + k, shot0=0, B=1501)
+        prior = bpq.prior_tensor(t, *ch)
+        for max_iter, B in ((60, 1501), (1, 333), (60, 1)):
+            s = syn[:B].contiguous()
+            t.set_serial_shots_per_warp(1)
+            one = bpq.decode(t, s, prior, variant, max_iter=max_iter, schedule="serial")
+            t.set_serial_shots_per_warp(2)
+            two = bpq.decode(t, s, prior, variant, max_iter=max_iter, schedule="serial")
+            t.set_serial_shots_per_warp(0)
+            for x, y in zip(one, two):
+                assert torch.equal(x, y), (t.N, variant, max_iter, B)
+
