@@ -303,8 +303,11 @@ int bpq_decode_serial(const bpq_tanner *t, const uint32_t *syn_dev, const float 
  * two, its lanes working on the same qubit of both, whose messages share
  * 64-bit shared-memory slots and packed f32x2 arithmetic (each shot stops on
  * its own and the warp takes the next one for that half); 0 = automatic (2
- * once the batch holds at least 4 shots per resident one-shot warp, e.g.
- * 9120 toric d = 15 shots on a GB300).  The trace keeps one shot per warp.
+ * where shared memory still holds 16 two-shot warps per SM and the batch
+ * holds at least 128 shots per resident one-shot warp, e.g. 622592 planar
+ * d = 7 shots on a GB300; the kernel is latency-bound, so codes whose
+ * two-shot warps fill shared memory sooner, such as toric d = 15, keep one
+ * shot per warp).  The trace keeps one shot per warp.
  * Errors: EINVAL (a value outside 0..2); bpq_decode_serial returns EINVAL
  * for 2 when two shots of the code do not fit in shared memory. */
 int bpq_set_serial_shots_per_warp(bpq_tanner *t, int shots_per_warp);

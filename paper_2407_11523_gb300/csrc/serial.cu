@@ -96,15 +96,22 @@ int serial_launch(const bpq_tanner *t, const uint32_t *syn, const float *prior, 
     layout(1);
     if (fixed + a.warp_bytes > limit) return fail(BPQ_EINVAL, "code too large for the serial kernel's shared memory");
     const long warps1 = (long)std::min<size_t>(32, (limit - fixed) / a.warp_bytes);
-    // two shots per warp (not for traces): on request, or automatically once
-    // the batch gives every resident one-shot warp kSerialPairShots shots
+    // two shots per warp (not for traces): on request, or automatically where
+    // shared memory still holds kSerialPairWarps two-shot warps per SM and the
+    // batch gives every resident one-shot warp kSerialPairShots shots.  The
+    // kernel is latency-bound: with fewer warps the two-shot kernel's shorter
+    // instruction stream per shot does not make up for the lost warps (toric
+    // d = 15 on GB300: 7 two-shot warps, 2.26e7 against 2.53e7 shots/s at
+    // 1e5 shots, 3.2e7 against 3.3e7 at 1e6), and small batches, whose time
+    // is set by their slowest shots, finish sooner with one shot per warp.
     bool pairs = false;
     if (!trace) {
         layout(2);
         const bool fits = fixed + a.warp_bytes <= limit;
         const int k = t->serial_shots_per_warp;
         if (k == 2 && !fits) return fail(BPQ_EINVAL, "two shots per warp do not fit in shared memory for this code");
-        pairs = fits && (k == 2 || (k == 0 && (long)B >= kSerialPairShots * warps1 * t->num_sms));
+        const bool full_occupancy = fits && (limit - fixed) / a.warp_bytes >= (size_t)sk::kSerialPairWarps;
+        pairs = fits && (k == 2 || (k == 0 && full_occupancy && (long)B >= kSerialPairShots * warps1 * t->num_sms));
         if (!pairs) layout(1);
     }
     int warps = (int)std::min<size_t>(pairs ? sk::kSerialPairWarps : 32, (limit - fixed) / a.warp_bytes);

@@ -645,7 +645,9 @@ SerialKernelFn pick_serial_pair(int variant, int layout);  // layout: 0 generic,
 }  // namespace sk
 
 // Two shots per warp are chosen automatically from this many shots per
-// resident one-shot warp.
-constexpr long kSerialPairShots = 4;
+// resident one-shot warp (where shared memory holds kSerialPairWarps
+// two-shot warps per SM; planar d = 7 on GB300: 1.14e8 one-shot against
+// 1.23e8 two-shot EWAInit-BP shots/s at 1e6 shots, 7.0e7 against 6.3e7 at 1e5).
+constexpr long kSerialPairShots = 128;
 
 }  // namespace bpq

@@ -155,49 +155,65 @@ int build_tables(bpq_tanner *t) {
 }
 
 namespace {
-// Message slots of the serial kernel's edges: slot = bank + 32 * row, with
+// Message slots of the serial kernels' edges: slot = bank + 32 * row, with
 // bank chosen greedily so that the edges one warp instruction touches (the
 // k-th edge, or its check's r-th other edge, of the qubits of one 32-lane
-// step of a level) fall in distinct banks where possible.  Edges are
+// step of a level) fall in distinct banks where possible: distinct slots
+// mod 32 across the warp (32-bit accesses of the one-shot kernel) and
+// distinct slots mod 16 within each half-warp (the 64-bit slot accesses of
+// the two-shot kernel are served half a warp at a time).  Edges are
 // coloured in sweep order; each bank holds at most ceil(E / 32) + 1 edges.
 std::vector<int> colour_serial_slots(const std::vector<std::array<int, 4>> &at, const std::vector<int> &edge_chk,
                                      const std::vector<int32_t> &chk_ptr, const std::vector<int> &order,
                                      const std::vector<int> &lp, int E, int *nslots) {
     const int nlev = (int)lp.size() - 1;
-    std::vector<std::vector<int>> groups;
+    struct Use {
+        int edge, lane;
+    };
+    std::vector<std::vector<Use>> groups;
     for (int l = 0; l < nlev; ++l)
         for (int s0 = lp[l]; s0 < lp[l + 1]; s0 += 32) {
             const int s1 = std::min(lp[l + 1], s0 + 32);
             for (int k = 0; k < 4; ++k)
                 for (int r = 0; r < 4; ++r) {
-                    std::vector<int> g;
+                    std::vector<Use> g;
                     for (int v = s0; v < s1; ++v) {
                         const int e = at[order[v]][k];
                         if (e < 0) continue;
                         const int i = edge_chk[e];
                         if (r == 3) {
-                            g.push_back(e);
+                            g.push_back({e, v - s0});
                             continue;
                         }
                         int f = 0;
                         for (int x = chk_ptr[i]; x < chk_ptr[i + 1]; ++x)
-                            if (x != e && f++ == r) g.push_back(x);
+                            if (x != e && f++ == r) g.push_back({x, v - s0});
                     }
                     if (!g.empty()) groups.push_back(std::move(g));
                 }
         }
-    std::vector<std::vector<int>> edge_groups(E);
+    struct Member {
+        int group, lane;
+    };
+    std::vector<std::vector<Member>> edge_groups(E);  // the groups of an edge, with its lane in each
     for (int gi = 0; gi < (int)groups.size(); ++gi)
-        for (int e : groups[gi]) edge_groups[e].push_back(gi);
+        for (const Use &u : groups[gi]) edge_groups[u.edge].push_back({gi, u.lane});
     const int cap = (E + 31) / 32 + 1;
     std::vector<int> bank(E, -1), fill(32, 0), slot(E);
     for (int v = 0; v < (int)order.size(); ++v)
         for (int e : at[order[v]]) {
             if (e < 0) continue;
             int cost[32] = {0};
-            for (int gi : edge_groups[e])
-                for (int x : groups[gi])
-                    if (bank[x] >= 0) ++cost[bank[x]];
+            for (const Member &eg : edge_groups[e])
+                for (const Use &u : groups[eg.group]) {
+                    const int b = bank[u.edge];
+                    if (b < 0) continue;
+                    ++cost[b];
+                    if ((u.lane < 16) == (eg.lane < 16)) {
+                        ++cost[b & 15];
+                        ++cost[(b & 15) + 16];
+                    }
+                }
             int best = -1;
             for (int b = 0; b < 32; ++b)
                 if (fill[b] < cap && (best < 0 || cost[b] < cost[best] || (cost[b] == cost[best] && fill[b] < fill[best])))
