@@ -63,6 +63,8 @@ def parse():
                          "aewa: EWAInit-BP vs AEWA-BP on planar L = 3, 7, 11 (Appendix C); "
                          "serial: serial vs parallel schedule on planar d=7 and toric d=15")
     ap.add_argument("--loads", default="1e4,1e5,1e6,1e7", help="offered loads (requests/s) for --workload serve")
+    ap.add_argument("--train-loss", default="coset", choices=["coset", "posterior"],
+                    help="train: coset (every iteration's checks and logicals) or posterior (final cross-entropy)")
     ap.add_argument("--train-model", default="ewainit", choices=["ewainit", "momentum"],
                     help="unrolled model for --workload train")
     ap.add_argument("--shots-per-thread", type=int, default=0, choices=[0, 1, 2],
@@ -893,7 +895,8 @@ def run_train(args, rank, world):
     def step():
         err, syn = next(it)
         opt.zero_grad()
-        L = bpq.unrolled_loss(t, syn, err, prior, a, b, w, T=T, ckpt_every=K, model=model, gamma=g)
+        L = bpq.unrolled_loss(t, syn, err, prior, a, b, w, T=T, ckpt_every=K, model=model, gamma=g,
+                              loss=args.train_loss)
         L.backward()
         opt.step()
         with torch.no_grad():
@@ -944,9 +947,10 @@ def run_train(args, rank, world):
     with torch.no_grad():
         g0 = torch.zeros_like(a) if mom else None
         gt = g.detach() if mom else None
-        Qtr, Ltr = bpq.unrolled_posterior(t, syn_t, err_t, prior, a, b, w, T=T, model=model, gamma=gt)
+        Qtr, Ltr = bpq.unrolled_posterior(t, syn_t, err_t, prior, a, b, w, T=T, model=model, gamma=gt,
+                                          loss=args.train_loss)
         Q0, L0 = bpq.unrolled_posterior(t, syn_t, err_t, prior, torch.full_like(a, 0.5), torch.zeros_like(b),
-                                        torch.ones_like(w), T=T, model=model, gamma=g0)
+                                        torch.ones_like(w), T=T, model=model, gamma=g0, loss=args.train_loss)
         ler_ee = {"trained": ler_early_exit(a.detach(), b.detach(), w.detach(), gt),
                   "untrained": ler_early_exit(torch.full_like(a, 0.5), torch.zeros_like(b), torch.ones_like(w), g0)}
     est_k, conv_k, _ = bpq.decode(t, syn_t, prior, model, max_iter=T, alpha=0.5, **({"gamma": 0.0} if mom else {}))
@@ -962,7 +966,8 @@ def run_train(args, rank, world):
                                        f"prior p={p0:.3f}; "
                                        "trainable alpha_t, beta_t" + (", gamma_t" if mom else "") +
                                        " (T each) and w_e (E); Adam lr 0.01, a fresh Philox batch every step, "
-                                       "108 steps", "model": model},
+                                       f"{args.warmup + args.steps + 100} steps", "model": model,
+                           "loss": args.train_loss},
                 "train_loss_first_last": [losses[0], losses[-1]],
                 "held_out_loss": {"trained": float(Ltr), "untrained": float(L0)},
                 "held_out_ler": {"trained_unrolled": ler_from_Q(Qtr), "untrained_unrolled": ler_from_Q(Q0),

@@ -483,8 +483,19 @@ void bpq_server_free(bpq_server *s);
  * beta_t m^(t-1) and scale each check-to-variable message by a weight w_e
  * (E weights in the check-major edge order of bpq_tanner_export).  Constant
  * alpha (and gamma), beta_t = 0, w_e = 1 is EWAInit-BP (Momentum-BP).
- * Loss: the mean over shots and qubits of -log softmax(0, -Q_X, -Q_Y,
- * -Q_Z)[true Pauli] of the final posterior.  Inputs: syn_dev [B][ceil(M/32)],
+ * Loss (loss may be NULL: the posterior loss):
+ *   BPQ_TRAIN_LOSS_POSTERIOR: the mean over shots and qubits of -log
+ *     softmax(0, -Q_X, -Q_Y, -Q_Z)[true Pauli] of the final posterior;
+ *   BPQ_TRAIN_LOSS_COSET: the mean over shots and iterations t = 1..T of
+ *     mean_i -log P_t(<E^, H_i> = s_i) + mean_L -log P_t(<E^, L> = <E, L>)
+ *     over the checks H_i and the caller's logical operators L
+ *     (logicals_dev [n_logicals][N] Pauli codes, 1..4 of them, e.g.
+ *     bpq_tanner_logicals), where E^ follows the product of iteration t's
+ *     posterior marginals (P(W) proportional to e^{-Q_W}, Q_I = 0) and E is
+ *     the true error: the probability that every iteration's soft decision
+ *     satisfies the syndrome and lies in the true error's coset (P taken at
+ *     least 1e-30, with no gradient below).
+ * Inputs: syn_dev [B][ceil(M/32)],
  * err_dev [B][N] Pauli codes (the true errors), prior_dev [N][3];
  * alpha_dev, beta_dev, gamma_dev [T] (gamma ignored, may be NULL, for
  * EWAInit), w_dev [E] (device float).  Codes of up to 1024 nodes; T <= 255.
@@ -497,16 +508,23 @@ void bpq_server_free(bpq_server *s);
  * too small a workspace, a checkpoint segment too long for shared memory),
  * ESTATE, ECUDA. */
 enum bpq_train_model { BPQ_TRAIN_EWAINIT = 0, BPQ_TRAIN_MOMENTUM = 1 };
+enum bpq_train_loss_kind { BPQ_TRAIN_LOSS_POSTERIOR = 0, BPQ_TRAIN_LOSS_COSET = 1 };
+typedef struct {
+    int kind;                     /* bpq_train_loss_kind */
+    const uint8_t *logicals_dev;  /* coset loss: [n_logicals][N] Pauli codes (device) */
+    int n_logicals;               /* coset loss: 1..4 */
+} bpq_train_loss;
 size_t bpq_train_workspace_bytes(const bpq_tanner *t, int model, int B, int T, int ckpt_every);
 int bpq_train_forward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
                       const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
                       const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
-                      float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes, void *stream);
+                      const bpq_train_loss *loss, float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes,
+                      void *stream);
 int bpq_train_backward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
                        const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
                        const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
-                       float *grad_alpha_dev, float *grad_beta_dev, float *grad_gamma_dev, float *grad_w_dev,
-                       void *work_dev, size_t work_bytes, void *stream);
+                       const bpq_train_loss *loss, float *grad_alpha_dev, float *grad_beta_dev,
+                       float *grad_gamma_dev, float *grad_w_dev, void *work_dev, size_t work_bytes, void *stream);
 
 /* ---------------------------------------------------------------- evaluation */
 

@@ -29,10 +29,14 @@ and the same beta_t, w_e; alpha_t = alpha, gamma_t = gamma, beta_t = 0,
 w_e = 1 is Momentum-BP.  In both models the v->c message is lambda of the
 posterior minus the edge's own message (eq. (mombp5); for EWAInit this is
 eq. (v_update), since Q = Pi^(t) + S).
-Messages are clipped to [-clip, clip] as in the decoder.  The loss is the
+Messages are clipped to [-clip, clip] as in the decoder.  Two losses: the
 cross-entropy of the final posterior against the true error, averaged over
-qubits and shots: per qubit the log-probabilities of (I, X, Y, Z) are
-log softmax(0, -Q_X, -Q_Y, -Q_Z), since Q_W = ln P(I)/P(W).
+qubits and shots (per qubit the log-probabilities of (I, X, Y, Z) are
+log softmax(0, -Q_X, -Q_Y, -Q_Z), since Q_W = ln P(I)/P(W)); and the coset
+loss (coset_loss): for every iteration, -log of the probability, under the
+product of the posterior marginals, that the estimate satisfies each check's
+syndrome bit and has the true error's parity with each logical operator,
+averaged over checks, logicals, iterations and shots.
 """
 from __future__ import annotations
 
@@ -83,10 +87,10 @@ def phi(x: torch.Tensor) -> torch.Tensor:
 
 
 def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0, model: str = "ewainit",
-            gamma=None):
-    """Q^(T) (B, N, 3) of the unrolled decoder.  syn: (B, M) 0/1; prior:
-    (N, 3) probabilities; alpha, beta (and gamma for model "momentum"):
-    (T,); w: (E,)."""
+            gamma=None, every: bool = False):
+    """Q^(T) (B, N, 3) of the unrolled decoder (every=True: the list of
+    Q^(1) .. Q^(T)).  syn: (B, M) 0/1; prior: (N, 3) probabilities; alpha,
+    beta (and gamma for model "momentum"): (T,); w: (E,)."""
     syn = torch.as_tensor(np.asarray(syn), dtype=torch.float64)
     prior = torch.as_tensor(np.asarray(prior), dtype=torch.float64)
     B = syn.shape[0]
@@ -96,6 +100,7 @@ def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0, mo
     v2c = lam(Pi0[g.var].expand(B, g.E, 3), g.own, g.anti).clamp(-clip, clip)   # eq. (init)
     Qprev = Pi0.expand(B, g.N, 3)
     Q = Qprev
+    Qs = []
     gm = torch.zeros(B, g.N, 3, dtype=torch.float64)
     for t in range(T):
         Pit = Pi0 if t == 0 else alpha[t] * Pi0 + (1.0 - alpha[t]) * Qprev
@@ -121,7 +126,8 @@ def forward(g: Graph, syn, prior, alpha, beta, w, T: int, clip: float = 30.0, mo
         new = lam(q_own, g.own, g.anti).clamp(-clip, clip)
         v2c = (1.0 - beta[t]) * new + beta[t] * v2c
         Qprev = Q
-    return Q
+        Qs.append(Q)
+    return Qs if every else Q
 
 
 def loss(Q: torch.Tensor, err) -> torch.Tensor:
@@ -133,16 +139,72 @@ def loss(Q: torch.Tensor, err) -> torch.Tensor:
     return -logp.gather(-1, err[..., None]).squeeze(-1).mean()
 
 
+MIN_PROB = 1e-30  # -log P is taken of max(P, MIN_PROB)
+
+
+def parity_distribution(ca: torch.Tensor) -> torch.Tensor:
+    """(P(even), P(odd)) of the sum mod 2 of independent bits, from each
+    bit's (P(0), P(1)) along dimension -2: the convolution over the bits in
+    order, (e, o) <- (e c + o a, e a + o c)."""
+    eo = torch.stack([torch.ones_like(ca[..., 0, 0]), torch.zeros_like(ca[..., 0, 0])], -1)
+    for j in range(ca.shape[-2]):
+        c, a = ca[..., j, 0], ca[..., j, 1]
+        eo = torch.stack([eo[..., 0] * c + eo[..., 1] * a, eo[..., 0] * a + eo[..., 1] * c], -1)
+    return eo
+
+
+def coset_loss(Qs, H, syn, err, logicals) -> torch.Tensor:
+    """Mean over shots and iterations of
+        mean_i -log P(<E^, H_i> = s_i) + mean_L -log P(<E^, L> = <E, L>),
+    E^ distributed as the product of the iteration's posterior marginals
+    (P(W) proportional to e^{-Q_W}, Q_I = 0; Q_W = ln P(I)/P(W)) and E the
+    true error: each operator's parity distribution is the convolution over
+    its support of (P(E^_j commutes with R_j), P(it anticommutes)).
+    Qs: list of (B, N, 3); H: (M, N) and logicals: (n, N) Pauli codes;
+    syn: (B, M) 0/1; err: (B, N) Pauli codes."""
+    H = np.asarray(H)
+    Lg = np.asarray(logicals)
+    err = np.asarray(err)
+    target_l = np.stack([(_anti(err, Lg[l][None, :])).sum(-1) % 2 for l in range(Lg.shape[0])], -1)   # (B, n)
+    groups = [(H, torch.as_tensor(np.asarray(syn), dtype=torch.long)),
+              (Lg, torch.as_tensor(target_l, dtype=torch.long))]
+    total = 0.0
+    for Q in Qs:
+        logits = torch.cat([torch.zeros_like(Q[..., :1]), -Q], -1)
+        pi = torch.softmax(logits, -1)                                          # (B, N, 4): I, X, Y, Z
+        term = 0.0
+        for R, target in groups:
+            rows = []
+            for r in range(R.shape[0]):
+                supp = np.nonzero(R[r])[0]
+                an = torch.as_tensor(np.stack([_anti(np.full(supp.size, w), R[r, supp]) for w in (1, 2, 3)], -1)
+                                     .astype(np.float64))                      # (w, 3): W anticommutes with R_j
+                p = pi[:, supp, 1:]                                             # (B, w, 3)
+                a = (p * an).sum(-1)
+                c = pi[:, supp, 0] + (p * (1.0 - an)).sum(-1)
+                rows.append(parity_distribution(torch.stack([c, a], -1)))      # (B, 2)
+            eo = torch.stack(rows, 1)                                           # (B, rows, 2)
+            P = eo.gather(-1, target[..., None]).squeeze(-1)
+            term = term + (-torch.log(P.clamp_min(MIN_PROB))).mean(-1)
+        total = total + term
+    return (total / len(Qs)).mean()
+
+
 def loss_and_grads(H, syn, err, prior, alpha, beta, w, T: int, clip: float = 30.0, model: str = "ewainit",
-                   gamma=None):
+                   gamma=None, kind: str = "posterior", logicals=None):
     """(loss, d loss / d alpha, d beta, d w) in float64 by autograd; for
-    model "momentum" also d loss / d gamma, as a fifth element."""
+    model "momentum" also d loss / d gamma, as a fifth element.  kind
+    "posterior" (loss) or "coset" (coset_loss with `logicals`)."""
     g = Graph(H)
     a = torch.tensor(np.asarray(alpha, dtype=np.float64), requires_grad=True)
     b = torch.tensor(np.asarray(beta, dtype=np.float64), requires_grad=True)
     ww = torch.tensor(np.asarray(w, dtype=np.float64), requires_grad=True)
     gm = None if gamma is None else torch.tensor(np.asarray(gamma, dtype=np.float64), requires_grad=True)
-    L = loss(forward(g, syn, prior, a, b, ww, T, clip, model=model, gamma=gm), err)
+    if kind == "coset":
+        L = coset_loss(forward(g, syn, prior, a, b, ww, T, clip, model=model, gamma=gm, every=True), H, syn, err,
+                       logicals)
+    else:
+        L = loss(forward(g, syn, prior, a, b, ww, T, clip, model=model, gamma=gm), err)
     L.backward()
     out = (float(L), a.grad.numpy(), b.grad.numpy(), ww.grad.numpy())
     if model == "momentum":

@@ -96,8 +96,9 @@ def lib():
             "bpq_server_create_slots": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, P, sz, PP]),
             "bpq_server_free": (None, [P]),
             "bpq_train_workspace_bytes": (sz, [P, i, i, i, i]),
-            "bpq_train_forward": (i, [P, i, P, P, P, i, i, i, P, P, P, P, ctypes.c_float, P, P, P, sz, P]),
-            "bpq_train_backward": (i, [P, i, P, P, P, i, i, i, P, P, P, P, ctypes.c_float, P, P, P, P, P, sz, P]),
+            "bpq_train_forward": (i, [P, i, P, P, P, i, i, i, P, P, P, P, ctypes.c_float, P, P, P, P, sz, P]),
+            "bpq_train_backward": (i, [P, i, P, P, P, i, i, i, P, P, P, P, ctypes.c_float, P, P, P, P, P, P, sz,
+                                       P]),
             "bpq_last_error": (ctypes.c_char_p, []),
             "bpq_version": (i, []),
         }
@@ -590,13 +591,32 @@ class Server:
 TRAIN_MODELS = {"ewainit": 0, "momentum": 1}
 
 
+class TrainLoss(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("logicals_dev", ctypes.c_void_p), ("n_logicals", ctypes.c_int)]
+
+
+TRAIN_LOSSES = {"posterior": 0, "coset": 1}
+
+
+def _train_loss(tanner, kind, logicals, device):
+    """bpq_train_loss for `kind`; the coset loss takes logical operators
+    (n, N) Pauli codes, by default the tanner's own (bpq_tanner_logicals).
+    Returns (struct, tensor keeping the device copy alive)."""
+    k = TRAIN_LOSSES[kind]
+    if k == 0:
+        return TrainLoss(0, None, 0), None
+    L = tanner.logicals() if logicals is None else np.asarray(logicals, dtype=np.uint8)
+    Ld = torch.as_tensor(np.ascontiguousarray(L, dtype=np.uint8), device=device)
+    return TrainLoss(k, Ld.data_ptr(), int(L.shape[0])), Ld
+
+
 class _Unrolled(torch.autograd.Function):
     """Loss of an unrolled decoder (model EWAInit or Momentum) as a function
     of its parameters (alpha, beta, w, gamma); forward and backward run in
     libbpq's CUDA kernels (bpq_train_forward / bpq_train_backward)."""
 
     @staticmethod
-    def forward(ctx, alpha, beta, w, gamma, model, tanner, syn, err, prior, T, ckpt_every, msg_clip):
+    def forward(ctx, alpha, beta, w, gamma, model, tanner, syn, err, prior, T, ckpt_every, msg_clip, lossdef):
         alpha, beta, w = alpha.contiguous().float(), beta.contiguous().float(), w.contiguous().float()
         gamma = gamma.contiguous().float() if gamma is not None else None
         B = syn.shape[0]
@@ -605,10 +625,11 @@ class _Unrolled(torch.autograd.Function):
         loss = torch.empty(1, dtype=torch.float32, device=syn.device)
         _check(lib().bpq_train_forward(tanner.handle, model, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every,
                                        _ptr(alpha), _ptr(beta), _ptr(gamma) if gamma is not None else None, _ptr(w),
-                                       msg_clip, _ptr(loss), None, _ptr(work), nbytes, _stream(None)),
+                                       msg_clip, ctypes.byref(lossdef[0]), _ptr(loss), None, _ptr(work), nbytes,
+                                       _stream(None)),
                "bpq_train_forward")
         ctx.save_for_backward(alpha, beta, w, *( [gamma] if gamma is not None else []))
-        ctx.rest = (model, tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes)
+        ctx.rest = (model, tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes, lossdef)
         return loss[0]
 
     @staticmethod
@@ -616,44 +637,52 @@ class _Unrolled(torch.autograd.Function):
         saved = ctx.saved_tensors
         alpha, beta, w = saved[:3]
         gamma = saved[3] if len(saved) > 3 else None
-        model, tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes = ctx.rest
+        model, tanner, syn, err, prior, T, ckpt_every, msg_clip, work, nbytes, lossdef = ctx.rest
         ga, gb, gw = torch.empty_like(alpha), torch.empty_like(beta), torch.empty_like(w)
         gg = torch.empty_like(gamma) if gamma is not None else None
         _check(lib().bpq_train_backward(tanner.handle, model, _ptr(syn), _ptr(err), _ptr(prior), syn.shape[0], T,
                                         ckpt_every, _ptr(alpha), _ptr(beta),
-                                        _ptr(gamma) if gamma is not None else None, _ptr(w), msg_clip, _ptr(ga),
-                                        _ptr(gb), _ptr(gg) if gg is not None else None, _ptr(gw), _ptr(work), nbytes,
+                                        _ptr(gamma) if gamma is not None else None, _ptr(w), msg_clip,
+                                        ctypes.byref(lossdef[0]), _ptr(ga), _ptr(gb),
+                                        _ptr(gg) if gg is not None else None, _ptr(gw), _ptr(work), nbytes,
                                         _stream(None)), "bpq_train_backward")
         return (ga * gout, gb * gout, gw * gout, gg * gout if gg is not None else None,
-                None, None, None, None, None, None, None, None)
+                None, None, None, None, None, None, None, None, None)
 
 
 def unrolled_loss(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0,
-                  model="ewainit", gamma=None):
+                  model="ewainit", gamma=None, loss="posterior", logicals=None):
     """Differentiable loss of the unrolled decoder (see bpq_train_forward):
     model "ewainit" (EWA weights alpha) or "momentum" (steps alpha, rates
-    gamma); gradients flow to alpha (T,), beta (T,), w (E,) and gamma (T,)."""
+    gamma); loss "posterior" (cross-entropy of the final posterior) or
+    "coset" (every iteration's soft decision in the syndrome's and the true
+    error's coset, with logical operators `logicals`, by default the
+    tanner's); gradients flow to alpha (T,), beta (T,), w (E,) and gamma
+    (T,)."""
     tanner.upload()
     m = TRAIN_MODELS[model]
     if m == 1 and gamma is None:
         raise BPQError("the Momentum model needs gamma")
+    lossdef = _train_loss(tanner, loss, logicals, syn.device)
     return _Unrolled.apply(alpha, beta, w, gamma if m == 1 else None, m, tanner, syn, err, prior, T, ckpt_every,
-                           msg_clip)
+                           msg_clip, lossdef)
 
 
 def unrolled_posterior(tanner: Tanner, syn, err, prior, alpha, beta, w, T=25, ckpt_every=5, msg_clip=30.0,
-                       model="ewainit", gamma=None):
+                       model="ewainit", gamma=None, loss="posterior", logicals=None):
     """Final posterior Q^(T) (B, N, 3) and the loss of the unrolled decoder."""
     tanner.upload()
     m = TRAIN_MODELS[model]
     B = syn.shape[0]
     nbytes = lib().bpq_train_workspace_bytes(tanner.handle, m, B, T, ckpt_every)
     work = torch.empty(nbytes, dtype=torch.uint8, device=syn.device)
-    loss = torch.empty(1, dtype=torch.float32, device=syn.device)
+    out = torch.empty(1, dtype=torch.float32, device=syn.device)
     Q = torch.empty((B, tanner.N, 3), dtype=torch.float32, device=syn.device)
     a, b, ww = alpha.contiguous().float(), beta.contiguous().float(), w.contiguous().float()
     g = gamma.contiguous().float() if gamma is not None else None
+    lossdef = _train_loss(tanner, loss, logicals, syn.device)
     _check(lib().bpq_train_forward(tanner.handle, m, _ptr(syn), _ptr(err), _ptr(prior), B, T, ckpt_every, _ptr(a),
-                                   _ptr(b), _ptr(g) if g is not None else None, _ptr(ww), msg_clip, _ptr(loss),
-                                   _ptr(Q), _ptr(work), nbytes, _stream(None)), "bpq_train_forward")
-    return Q, loss[0]
+                                   _ptr(b), _ptr(g) if g is not None else None, _ptr(ww), msg_clip,
+                                   ctypes.byref(lossdef[0]), _ptr(out), _ptr(Q), _ptr(work), nbytes, _stream(None)),
+           "bpq_train_forward")
+    return Q, out[0]

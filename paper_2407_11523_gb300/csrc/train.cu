@@ -16,7 +16,22 @@
 //   m_c->v^(t)  = clip(w_e (-1)^{s_i} r_e),  r_e = 2 atanh prod_{f != e} tanh(m_v->c^(t-1)_f / 2)
 //   S^(t)       = sum of anticommuting m_c->v^(t)
 //   m_v->c^(t)  = (1 - beta_t) clip(lambda_H(Q^(t) - own message)) + beta_t m_v->c^(t-1)
-//   loss        = mean over shots and qubits of -log softmax(0, -Q_X, -Q_Y, -Q_Z)[true Pauli]
+//
+// Two losses:
+//   posterior:  mean over shots and qubits of -log softmax(0, -Q_X, -Q_Y, -Q_Z)[true Pauli]
+//               of the final posterior Q^(T);
+//   coset:      mean over shots and iterations t = 1..T of
+//                 mean over checks i of -log P_t(<E^, H_i> = s_i)
+//               + mean over logical operators L of -log P_t(<E^, L> = <E, L>),
+//               where E^ is drawn from the product of the posterior marginals
+//               of iteration t (pi_W proportional to e^{-Q_W}, Q_I = 0) and E is
+//               the true error: the probability that the soft decision of every
+//               iteration satisfies the syndrome and lies in the true error's
+//               coset (neural-BP decoders for quantum codes train on this kind
+//               of loss).  The parity distribution of a check or logical is the
+//               (P(even), P(odd)) convolution over its qubits of each qubit's
+//               (commute, anticommute) probabilities, sums of positive terms, so
+//               small probabilities keep their relative accuracy.
 //
 // At constant alpha (and gamma), beta_t = 0, w_e = 1 the forward pass is
 // EWAInit-BP (Momentum-BP).  One CTA decodes one shot (thread x owns check
@@ -43,6 +58,9 @@ namespace bpq {
 namespace tr {
 
 constexpr int kEWAInit = BPQ_TRAIN_EWAINIT, kMomentum = BPQ_TRAIN_MOMENTUM;
+constexpr int kCoset = BPQ_TRAIN_LOSS_COSET;
+constexpr int kMaxLogicals = 4;
+constexpr float kMinProb = 1e-30f;  // -log P is taken of max(P, kMinProb); no gradient below
 
 struct TrainArgs {
     const uint8_t *table;
@@ -55,6 +73,9 @@ struct TrainArgs {
     int ck_floats;     // floats per checkpoint: 7 n_pad (EWAInit) or 10 n_pad (Momentum)
     int width;         // floats per gradient row: 2T + E (+ T for Momentum)
     float clip;
+    int loss_kind;     // BPQ_TRAIN_LOSS_POSTERIOR or BPQ_TRAIN_LOSS_COSET
+    const uint8_t *logicals;  // coset loss: [n_log][N] Pauli codes
+    int n_log;
     float *ckpt;       // [B][nck][ck_floats]: m_v->c (4 n_pad slots), Q (3 n_pad), g (3 n_pad)
     float *loss_shot;  // [B] sum over qubits of the cross-entropy
     float *Q_out;      // optional [B][N][3]
@@ -95,6 +116,68 @@ __device__ __forceinline__ float block_sum(float v, float *red) {
     if (threadIdx.x == 0)
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
     return s;  // valid on thread 0
+}
+
+// Sum of v over the CTA (two values), received by every thread.  red2:
+// 32 float2 of shared memory.
+__device__ __forceinline__ float2 block_sum2_all(float2 v, float2 *red2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float2 r = make_float2(0.f, 0.f);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        r.x += red2[k].x;
+        r.y += red2[k].y;
+    }
+    return r;
+}
+
+// Parity distribution (P(even), P(odd)) of the sum of two independent bits
+// with distributions x and y.
+__device__ __forceinline__ float2 parity_combine(float2 x, float2 y) {
+    return make_float2(x.x * y.x + x.y * y.y, x.x * y.y + x.y * y.x);
+}
+
+// Parity distribution of the bits of all threads of the CTA (each thread's
+// (P(even), P(odd)); (1, 0) for none), received by every thread.
+__device__ __forceinline__ float2 block_parity_all(float2 v, float2 *red2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = parity_combine(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float2 r = make_float2(1.f, 0.f);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = parity_combine(r, red2[k]);
+    return r;
+}
+
+// Posterior marginals (pi_I, pi_X, pi_Y, pi_Z) of a qubit: pi_W proportional
+// to e^{-Q_W}, Q_I = 0.
+__device__ __forceinline__ void marginals(const float (&Q)[3], float (&pi)[4]) {
+    const float c0 = fminf(0.f, fminf(Q[0], fminf(Q[1], Q[2])));
+    const float e[4] = {expf(c0), expf(c0 - Q[0]), expf(c0 - Q[1]), expf(c0 - Q[2])};
+    const float z = e[0] + e[1] + e[2] + e[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pi[k] = e[k] / z;
+}
+
+// (P(the qubit's error commutes with P), P(it anticommutes)), P in 1..3.
+__device__ __forceinline__ float2 comm_anti(const float (&pi)[4], uint32_t P) {
+    float c = pi[0], an = 0.f;
+#pragma unroll
+    for (int w = 1; w <= 3; ++w) {
+        if (anti((uint32_t)w, P))
+            an += pi[w];
+        else
+            c += pi[w];
+    }
+    return make_float2(c, an);
 }
 
 struct Adj {
@@ -148,19 +231,64 @@ __device__ __forceinline__ void check_forward(const TrainArgs &a, const Adj &d, 
 }
 
 // Forward: one CTA per shot.
+// Parities <E, L> of the true error with the logical operators (bit l),
+// the same on every thread.
+__device__ __forceinline__ uint32_t true_logical_parities(const TrainArgs &a, int x, int shot, float2 *red2) {
+    uint32_t tau = 0;
+    for (int l = 0; l < a.n_log; ++l) {
+        float v = 0.f;
+        if (x < a.N) v = anti(a.err[(size_t)shot * a.N + x], a.logicals[(size_t)l * a.N + x]) ? 1.f : 0.f;
+        const float n = block_sum2_all(make_float2(v, 0.f), red2).x;
+        tau |= ((uint32_t)n & 1u) << l;
+    }
+    return tau;
+}
+
+// Coset loss of one iteration for one shot (the thread's part; the CTA's
+// threads together hold mean_i -log P(<E^, H_i> = s_i) + mean_L -log P(<E^,
+// L> = <E, L>)).  pi: the thread's qubit's marginals (x < N); ub2: [S4]
+// float2 edge slots.
+__device__ __forceinline__ float coset_loss_forward(const TrainArgs &a, const Adj &d, int x, const float (&pi)[4],
+                                                    uint32_t tau, float2 *ub2, float2 *red2) {
+    if (x < a.N)
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t p = (d.vp >> (2 * k)) & 3u;
+            ub2[4 * x + k] = p ? comm_anti(pi, p) : make_float2(1.f, 0.f);
+        }
+    __syncthreads();
+    float part = 0.f;
+    if (x < a.M) {
+        float2 eo = make_float2(1.f, 0.f);
+        for (int n = 0; n < 4; ++n)
+            if ((d.cp >> (2 * n)) & 3u) eo = parity_combine(eo, ub2[d.sl[n]]);
+        part += -logf(fmaxf(d.sb ? eo.y : eo.x, kMinProb)) / (float)a.M;
+    }
+    for (int l = 0; l < a.n_log; ++l) {
+        const uint32_t P = x < a.N ? a.logicals[(size_t)l * a.N + x] : 0u;
+        const float2 eo = block_parity_all(P ? comm_anti(pi, P) : make_float2(1.f, 0.f), red2);
+        if (x == 0) part += -logf(fmaxf(((tau >> l) & 1u) ? eo.y : eo.x, kMinProb)) / (float)a.n_log;
+    }
+    return part;
+}
+
 template <int MODEL>
 __global__ void train_forward_kernel(const TrainArgs a) {
     extern __shared__ __align__(16) float sm[];
-    const int Np = a.n_pad;
-    float *v2c = sm;                  // [4Np + 4]
-    float *c2v = v2c + 4 * Np + 4;    // [4Np + 4]
-    float *Pi0 = c2v + 4 * Np + 4;    // [3Np]
-    float *Qp = Pi0 + 3 * Np;         // [3Np]
-    float *Gp = Qp + 3 * Np;          // [3Np] momentum g^(t-1) (Momentum only)
-    float *red = Gp + (MODEL == kMomentum ? 3 * Np : 0);  // [32]
+    const int Np = a.n_pad, S4 = 4 * Np + 4;
+    const bool coset = a.loss_kind == kCoset;
+    float2 *ub2 = reinterpret_cast<float2 *>(sm);  // [S4] edge parity distributions (coset loss only)
+    float *v2c = sm + (coset ? 2 * S4 : 0);       // [4Np + 4]
+    float *c2v = v2c + S4;                         // [4Np + 4]
+    float *Pi0 = c2v + S4;                         // [3Np]
+    float *Qp = Pi0 + 3 * Np;                      // [3Np]
+    float *Gp = Qp + 3 * Np;                       // [3Np] momentum g^(t-1) (Momentum only)
+    float *red = Gp + (MODEL == kMomentum ? 3 * Np : 0);  // [64]
+    float2 *red2 = reinterpret_cast<float2 *>(red);
     const int x = threadIdx.x, shot = blockIdx.x;
     Adj d;
     load_adj(a, x, shot, d);
+    const uint32_t tau = coset ? true_logical_parities(a, x, shot, red2) : 0u;
+    float coset_sum = 0.f;
     const uint32_t zero = 4u * (uint32_t)Np;
     if (x == 0) {
         v2c[zero] = 0.f;
@@ -232,40 +360,122 @@ __global__ void train_forward_kernel(const TrainArgs a) {
             for (int w = 0; w < 3; ++w) Qp[w * Np + x] = Q[w];
         }
         __syncthreads();
+        if (coset) {
+            float pi[4] = {1.f, 0.f, 0.f, 0.f};
+            if (x < a.N) marginals(Q, pi);
+            coset_sum += coset_loss_forward(a, d, x, pi, tau, ub2, red2);
+        }
     }
-    // cross-entropy of the final posterior against the true error
-    float ce = 0.f;
-    if (x < a.N) {
+    // cross-entropy of the final posterior against the true error (posterior
+    // loss), or the coset loss's mean over iterations
+    float ce = coset ? coset_sum / (float)a.T : 0.f;
+    if (x < a.N && !coset) {
         const float z[4] = {0.f, -Q[0], -Q[1], -Q[2]};
         const float zm = fmaxf(fmaxf(z[0], z[1]), fmaxf(z[2], z[3]));
         float se = 0.f;
         for (int k = 0; k < 4; ++k) se += expf(z[k] - zm);
         const int e = a.err[(size_t)shot * a.N + x];
         ce = zm + logf(se) - z[e];
-        if (a.Q_out)
-            for (int w = 0; w < 3; ++w) a.Q_out[((size_t)shot * a.N + x) * 3 + w] = Q[w];
     }
+    if (x < a.N && a.Q_out)
+        for (int w = 0; w < 3; ++w) a.Q_out[((size_t)shot * a.N + x) * 3 + w] = Q[w];
     const float tot = block_sum(ce, red);
     if (x == 0) a.loss_shot[shot] = tot;
 }
 
 // Backward: one CTA per shot; segments of K iterations recomputed from the
 // checkpoints into shared memory, adjoint in reverse.
+// Adds d (coset loss of iteration t) / d Q^(t) to Qbar (x < N): Qt = Q^(t)
+// [3][Np] in shared memory; ub2 [S4] float2 scratch.  Every thread calls it.
+// With P_match = (1 + sigma prod_j u_j) / 2 (u_j = c_j - a_j, sigma = +-1 the
+// target parity), d (-log P_match) / d u_j = -sigma U'_j / (2 P_match), U'_j
+// the product over the other qubits, and d u_j / d Q_W = 2 pi_W (c_j -
+// [W commutes with the operator's Pauli on j]).
+__device__ __forceinline__ void coset_loss_backward(const TrainArgs &a, const Adj &d, int x, const float *Qt,
+                                                    uint32_t tau, float2 *ub2, float2 *red2, float (&Qbar)[3]) {
+    const int Np = a.n_pad;
+    float pi[4] = {1.f, 0.f, 0.f, 0.f};
+    float2 ca[4];
+    if (x < a.N) {
+        const float Q[3] = {Qt[x], Qt[Np + x], Qt[2 * Np + x]};
+        marginals(Q, pi);
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t p = (d.vp >> (2 * k)) & 3u;
+            ca[k] = p ? comm_anti(pi, p) : make_float2(1.f, 0.f);
+            ub2[4 * x + k] = ca[k];
+        }
+    }
+    __syncthreads();
+    const float scale_c = 1.f / ((float)a.B * (float)a.T * (float)a.M);
+    const float scale_l = 1.f / ((float)a.B * (float)a.T * (float)a.n_log);
+    if (x < a.M) {
+        float2 in[4];
+        float2 eo = make_float2(1.f, 0.f);
+        for (int n = 0; n < 4; ++n) {
+            in[n] = ((d.cp >> (2 * n)) & 3u) ? ub2[d.sl[n]] : make_float2(1.f, 0.f);
+            eo = parity_combine(eo, in[n]);
+        }
+        const float P = d.sb ? eo.y : eo.x, sigma = d.sb ? -1.f : 1.f;
+        for (int n = 0; n < 4; ++n) {
+            if (!((d.cp >> (2 * n)) & 3u)) continue;
+            float U = 1.f;
+            for (int m = 0; m < 4; ++m)
+                if (m != n) U *= in[m].x - in[m].y;
+            ub2[d.sl[n]].x = P > kMinProb ? -sigma * U / P * scale_c : 0.f;
+        }
+    }
+    float gl[kMaxLogicals];
+    float2 cl[kMaxLogicals];
+    for (int l = 0; l < a.n_log; ++l) {
+        const uint32_t P = x < a.N ? a.logicals[(size_t)l * a.N + x] : 0u;
+        cl[l] = P ? comm_anti(pi, P) : make_float2(1.f, 0.f);
+        const float2 eo = block_parity_all(cl[l], red2);
+        const float u = cl[l].x - cl[l].y;
+        const float lg = P ? logf(fmaxf(fabsf(u), 1e-30f)) : 0.f, ng = (P && u < 0.f) ? 1.f : 0.f;
+        const float2 sums = block_sum2_all(make_float2(lg, ng), red2);
+        const float Pm = ((tau >> l) & 1u) ? eo.y : eo.x, sigma = ((tau >> l) & 1u) ? -1.f : 1.f;
+        gl[l] = 0.f;
+        if (P && Pm > kMinProb) {
+            const float U = ((int)(sums.y - ng) & 1 ? -1.f : 1.f) * expf(sums.x - lg);  // product over the others
+            gl[l] = -sigma * U / Pm * scale_l;
+        }
+    }
+    __syncthreads();
+    if (x < a.N) {
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t p = (d.vp >> (2 * k)) & 3u;
+            if (!p) continue;
+            const float g = ub2[4 * x + k].x;
+            for (int w = 0; w < 3; ++w) Qbar[w] += g * pi[w + 1] * (ca[k].x - (anti(w + 1, p) ? 0.f : 1.f));
+        }
+        for (int l = 0; l < a.n_log; ++l) {
+            const uint32_t P = a.logicals[(size_t)l * a.N + x];
+            if (!P) continue;
+            for (int w = 0; w < 3; ++w) Qbar[w] += gl[l] * pi[w + 1] * (cl[l].x - (anti(w + 1, P) ? 0.f : 1.f));
+        }
+    }
+    __syncthreads();  // ub2 is rewritten by the next iteration
+}
+
 template <int MODEL>
 __global__ void train_backward_kernel(const TrainArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int Np = a.n_pad, K = a.K, S4 = 4 * Np + 4;
-    float *Pi0 = sm;                                 // [3Np]
+    const bool coset = a.loss_kind == kCoset;
+    float2 *ub2 = reinterpret_cast<float2 *>(sm);   // [S4] (coset loss only)
+    float *Pi0 = sm + (coset ? 2 * S4 : 0);          // [3Np]
     float *vh = Pi0 + 3 * Np;                        // [(K+1)][S4]   m_v->c^(t0 .. t0+K)
     float *ch = vh + (size_t)(K + 1) * S4;           // [K][S4]       m_c->v^(t0+1 .. t0+K)
     float *Qh = ch + (size_t)K * S4;                 // [(K+1)][3Np]  Q^(t0 .. t0+K)
     float *gh = Qh + (size_t)(K + 1) * 3 * Np;       // [(K+1)][3Np]  g^(t0 .. t0+K) (Momentum only)
     float *vbar = gh + (MODEL == kMomentum ? (size_t)(K + 1) * 3 * Np : 0);  // [S4] adjoint of m_v->c^(t)
     float *cbar = vbar + S4;                         // [S4] adjoint of m_c->v^(t)
-    float *red = cbar + S4;                          // [32]
+    float *red = cbar + S4;                          // [64]
+    float2 *red2 = reinterpret_cast<float2 *>(red);
     const int x = threadIdx.x, shot = blockIdx.x;
     Adj d;
     load_adj(a, x, shot, d);
+    const uint32_t tau = coset ? true_logical_parities(a, x, shot, red2) : 0u;
     const uint32_t zero = 4u * (uint32_t)Np;
     if (x < a.N) {
         const float px = a.prior[3 * x], py = a.prior[3 * x + 1], pz = a.prior[3 * x + 2];
@@ -346,8 +556,8 @@ __global__ void train_backward_kernel(const TrainArgs a) {
             }
             __syncthreads();
         }
-        // ---- loss gradient at the last iteration ----
-        if (t1 == a.T && x < a.N) {
+        // ---- posterior loss: gradient at the last iteration ----
+        if (!coset && t1 == a.T && x < a.N) {
             const float *Q = Qh + (size_t)(t1 - t0) * 3 * Np;
             const float z[4] = {0.f, -Q[x], -Q[Np + x], -Q[2 * Np + x]};
             const float zm = fmaxf(fmaxf(z[0], z[1]), fmaxf(z[2], z[3]));
@@ -369,6 +579,8 @@ __global__ void train_backward_kernel(const TrainArgs a) {
             const float *Qprev = Qh + (size_t)(s - 1) * 3 * Np;
             const float al = a.alpha[t - 1], be = a.beta[t - 1];
             float bb = 0.f, ab = 0.f, gb = 0.f;
+            // coset loss: the gradient of iteration t's term joins Q^(t)'s adjoint
+            if (coset) coset_loss_backward(a, d, x, Qt, tau, ub2, red2, Qbar);
             // step A (qubit role): damping, lambda, posterior, EWA prior
             if (x < a.N) {
                 float Qacc[3] = {0.f, 0.f, 0.f}, cb_part[4] = {0.f, 0.f, 0.f, 0.f};
@@ -501,8 +713,8 @@ __global__ void reduce_rows_kernel(const float *rows, int B, int width, int offs
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int fill(const bpq_tanner *t, int model, const uint32_t *syn, const uint8_t *err, const float *prior, int B, int T,
-         int K, const float *alpha, const float *beta, const float *gamma, const float *w, float clip, void *work,
-         size_t work_bytes, TrainArgs &a) {
+         int K, const float *alpha, const float *beta, const float *gamma, const float *w, float clip,
+         const bpq_train_loss *loss, void *work, size_t work_bytes, TrainArgs &a) {
     int rc = need_uploaded(t);
     if (rc) return rc;
     if (model != kEWAInit && model != kMomentum) return fail(BPQ_EINVAL, "unknown training model");
@@ -510,6 +722,11 @@ int fill(const bpq_tanner *t, int model, const uint32_t *syn, const uint8_t *err
     if (!syn || !err || !prior || !alpha || !beta || !w || !work) return fail(BPQ_EINVAL, "NULL argument");
     if (model == kMomentum && !gamma) return fail(BPQ_EINVAL, "the Momentum model needs gamma");
     if (!(clip > 0.f)) return fail(BPQ_EINVAL, "msg_clip must be positive");
+    const int kind = loss ? loss->kind : BPQ_TRAIN_LOSS_POSTERIOR;
+    if (kind != BPQ_TRAIN_LOSS_POSTERIOR && kind != BPQ_TRAIN_LOSS_COSET) return fail(BPQ_EINVAL, "unknown loss");
+    if (kind == BPQ_TRAIN_LOSS_COSET && (!loss->logicals_dev || loss->n_logicals < 1 ||
+                                         loss->n_logicals > kMaxLogicals))
+        return fail(BPQ_EINVAL, "the coset loss needs 1 to 4 logical operators");
     if (std::max(t->N, t->M) > 1024) return fail(BPQ_EINVAL, "training kernels take codes of up to 1024 nodes");
     if (work_bytes < bpq_train_workspace_bytes(t, model, B, T, K))
         return fail(BPQ_EINVAL, "training workspace too small");
@@ -538,6 +755,9 @@ int fill(const bpq_tanner *t, int model, const uint32_t *syn, const uint8_t *err
     a.ck_floats = (model == kMomentum ? 10 : 7) * a.n_pad;
     a.width = (model == kMomentum ? 3 : 2) * T + t->E;
     a.clip = clip;
+    a.loss_kind = kind;
+    a.logicals = kind == BPQ_TRAIN_LOSS_COSET ? loss->logicals_dev : nullptr;
+    a.n_log = kind == BPQ_TRAIN_LOSS_COSET ? loss->n_logicals : 0;
     uint8_t *p = static_cast<uint8_t *>(work);
     a.ckpt = reinterpret_cast<float *>(p);
     p += a256(sizeof(float) * (size_t)B * a.nck * a.ck_floats);
@@ -568,33 +788,39 @@ size_t bpq_train_workspace_bytes(const bpq_tanner *t, int model, int B, int T, i
 int bpq_train_forward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
                       const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
                       const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
-                      float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes, void *stream) {
+                      const bpq_train_loss *loss, float *loss_dev, float *Q_dev, void *work_dev, size_t work_bytes,
+                      void *stream) {
     bpq::tr::TrainArgs a;
     int rc = bpq::tr::fill(t, model, syn_dev, err_dev, prior_dev, B, T, ckpt_every, alpha_dev, beta_dev, gamma_dev,
-                           w_dev, msg_clip, work_dev, work_bytes, a);
+                           w_dev, msg_clip, loss, work_dev, work_bytes, a);
     if (rc) return rc;
     if (!loss_dev) return fail(BPQ_EINVAL, "NULL loss output");
     a.Q_out = Q_dev;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool mom = model == BPQ_TRAIN_MOMENTUM;
-    const size_t smem = sizeof(float) * (2 * (4 * a.n_pad + 4) + (mom ? 9 : 6) * a.n_pad + 32);
+    const bool coset = a.loss_kind == BPQ_TRAIN_LOSS_COSET;
+    const size_t S4 = 4 * (size_t)a.n_pad + 4;
+    const size_t smem = sizeof(float) * ((coset ? 4 : 2) * S4 + (mom ? 9 : 6) * (size_t)a.n_pad + 64);
+    if (smem > 227 * 1024) return fail(BPQ_EINVAL, "code too large for the training kernels' shared memory");
     void (*fn)(const bpq::tr::TrainArgs) = mom ? bpq::tr::train_forward_kernel<bpq::tr::kMomentum>
                                                : bpq::tr::train_forward_kernel<bpq::tr::kEWAInit>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(BPQ_ECUDA, std::string("train forward attribute: ") + cudaGetErrorString(e));
     fn<<<B, bpq::tr::threads_for(t), smem, st>>>(a);
-    bpq::tr::reduce_rows_kernel<<<1, 32, 0, st>>>(a.loss_shot, B, 1, 0, 1, loss_dev, 1.f / ((float)B * (float)t->N));
+    // per-shot sums: over qubits (posterior loss) or already normalised (coset loss)
+    bpq::tr::reduce_rows_kernel<<<1, 32, 0, st>>>(a.loss_shot, B, 1, 0, 1, loss_dev,
+                                                  coset ? 1.f / (float)B : 1.f / ((float)B * (float)t->N));
     return bpq::cuda_check(cudaGetLastError(), "train forward launch");
 }
 
 int bpq_train_backward(const bpq_tanner *t, int model, const uint32_t *syn_dev, const uint8_t *err_dev,
                        const float *prior_dev, int B, int T, int ckpt_every, const float *alpha_dev,
                        const float *beta_dev, const float *gamma_dev, const float *w_dev, float msg_clip,
-                       float *grad_alpha_dev, float *grad_beta_dev, float *grad_gamma_dev, float *grad_w_dev,
-                       void *work_dev, size_t work_bytes, void *stream) {
+                       const bpq_train_loss *loss, float *grad_alpha_dev, float *grad_beta_dev,
+                       float *grad_gamma_dev, float *grad_w_dev, void *work_dev, size_t work_bytes, void *stream) {
     bpq::tr::TrainArgs a;
     int rc = bpq::tr::fill(t, model, syn_dev, err_dev, prior_dev, B, T, ckpt_every, alpha_dev, beta_dev, gamma_dev,
-                           w_dev, msg_clip, work_dev, work_bytes, a);
+                           w_dev, msg_clip, loss, work_dev, work_bytes, a);
     if (rc) return rc;
     const bool mom = model == BPQ_TRAIN_MOMENTUM;
     if (!grad_alpha_dev || !grad_beta_dev || !grad_w_dev || (mom && !grad_gamma_dev))
@@ -602,8 +828,9 @@ int bpq_train_backward(const bpq_tanner *t, int model, const uint32_t *syn_dev, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int K = a.K, Np = a.n_pad, S4 = 4 * Np + 4;
     const size_t hist = (size_t)(K + 1) * 3 * Np * (mom ? 2 : 1);
-    const size_t smem =
-        sizeof(float) * (3 * Np + (size_t)(K + 1) * S4 + (size_t)K * S4 + hist + 2 * S4 + 32);
+    const bool coset = a.loss_kind == BPQ_TRAIN_LOSS_COSET;
+    const size_t smem = sizeof(float) * ((coset ? 2 * (size_t)S4 : 0) + 3 * Np + (size_t)(K + 1) * S4 +
+                                         (size_t)K * S4 + hist + 2 * S4 + 64);
     if (smem > 227 * 1024) return fail(BPQ_EINVAL, "checkpoint interval too long for shared memory");
     void (*fn)(const bpq::tr::TrainArgs) = mom ? bpq::tr::train_backward_kernel<bpq::tr::kMomentum>
                                                : bpq::tr::train_backward_kernel<bpq::tr::kEWAInit>;

@@ -189,3 +189,87 @@ def test_momentum_backward_is_checkpoint_independent(bpq):
     for gk in grads[1:]:
         for g0, g1 in zip(grads[0], gk):
             assert torch.equal(g0, g1)
+
+
+# ---------------------------------------------------------------- coset loss
+
+
+@pytest.mark.parametrize("model,T,K", [("ewainit", 8, 5), ("ewainit", 25, 5), ("momentum", 12, 5)])
+def test_coset_loss_matches_oracle(bpq, model, T, K):
+    """The coset loss (every iteration's checks and logicals) against the
+    oracle's coset_loss, with the oracle's own logical operators passed to
+    the kernel."""
+    from oracle import codes
+    t, err, syn, prior, ch = setup(bpq, 32, 0.05, 21)
+    a, b, w = params(T, t.E, 22, spread=0.05)
+    gm = np.full(T, 0.3)
+    H, s, e, pri = oracle_inputs(t, err, syn, ch)
+    Lg = codes.logical_operators(H)
+    kw = dict(model=model, gamma=torch.tensor(gm, device="cuda", dtype=torch.float32) if model == "momentum" else None)
+    L = bpq.unrolled_loss(t, syn, err, prior, torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda"),
+                          torch.tensor(w, device="cuda"), T=T, ckpt_every=K, loss="coset", logicals=Lg, **kw)
+    Qs = unrolled.forward(unrolled.Graph(H), s, pri, torch.tensor(a), torch.tensor(b), torch.tensor(w), T,
+                          model=model, gamma=torch.tensor(gm) if model == "momentum" else None, every=True)
+    Lr = float(unrolled.coset_loss(Qs, H, s, e, Lg))
+    assert float(L) == pytest.approx(Lr, rel=2e-4)
+
+
+@pytest.mark.parametrize("model", ["ewainit", "momentum"])
+def test_coset_gradients_match_oracle_and_finite_differences(bpq, model):
+    from oracle import codes
+    T = 8
+    t, err, syn, prior, ch = setup(bpq, 8, 0.06, 23)
+    a, b, w = params(T, t.E, 24, spread=0.1)
+    gm = 0.3 + 0.05 * np.random.default_rng(25).standard_normal(T)
+    H, s, e, pri = oracle_inputs(t, err, syn, ch)
+    Lg = codes.logical_operators(H)
+    vals = (a, b, w) + ((gm,) if model == "momentum" else ())
+    ts = [torch.tensor(x, device="cuda", dtype=torch.float32, requires_grad=True) for x in vals]
+    L = bpq.unrolled_loss(t, syn, err, prior, ts[0], ts[1], ts[2], T=T, ckpt_every=5, model=model,
+                          gamma=ts[3] if model == "momentum" else None, loss="coset", logicals=Lg)
+    L.backward()
+    got = [x.grad.detach().cpu().numpy().astype(np.float64) for x in ts]
+    ref = unrolled.loss_and_grads(H, s, e, pri, a, b, w, T, model=model, gamma=gm if model == "momentum" else None,
+                                  kind="coset", logicals=Lg)
+    assert float(L) == pytest.approx(ref[0], rel=2e-4)
+    for g, r in zip(got, ref[1:]):
+        scale = np.abs(r).max()
+        assert np.abs(g - r).max() <= 2e-3 * scale + 1e-7, (np.abs(g - r).max(), scale)
+    g_ = unrolled.Graph(H)
+
+    def f(aa, ww):
+        Qs = unrolled.forward(g_, s, pri, torch.tensor(aa), torch.tensor(b), torch.tensor(ww), T, model=model,
+                              gamma=torch.tensor(gm) if model == "momentum" else None, every=True)
+        return float(unrolled.coset_loss(Qs, H, s, e, Lg))
+
+    h = 1e-6
+    for k in (1, T - 1):
+        dv = np.zeros(T); dv[k] = h
+        assert got[0][k] == pytest.approx((f(a + dv, w) - f(a - dv, w)) / (2 * h), rel=5e-3, abs=1e-6)
+    for k in (3, 100, t.E - 1):
+        dv = np.zeros(t.E); dv[k] = h
+        assert got[2][k] == pytest.approx((f(a, w + dv) - f(a, w - dv)) / (2 * h), rel=5e-3, abs=1e-6)
+
+
+def test_coset_backward_is_deterministic_and_checkpoint_independent(bpq):
+    t, err, syn, prior, ch = setup(bpq, 64, 0.07, 27)
+    T = 20
+    a, b, w = params(T, t.E, 28, spread=0.05)
+    grads = []
+    for K in (5, 5, 20, 7):
+        ts = [torch.tensor(x, device="cuda", dtype=torch.float32, requires_grad=True) for x in (a, b, w)]
+        bpq.unrolled_loss(t, syn, err, prior, *ts, T=T, ckpt_every=K, loss="coset").backward()
+        grads.append([x.grad.clone() for x in ts])
+    for gk in grads[1:]:
+        for g0, g1 in zip(grads[0], gk):
+            assert torch.equal(g0, g1)
+
+
+def test_coset_loss_refusals(bpq):
+    t, err, syn, prior, ch = setup(bpq, 4, 0.05, 29, d=5)
+    T = 4
+    args = (torch.full((T,), 0.5, device="cuda"), torch.zeros(T, device="cuda"), torch.ones(t.E, device="cuda"))
+    with pytest.raises(bpq.BPQError):
+        bpq.unrolled_loss(t, syn, err, prior, *args, T=T, loss="coset", logicals=np.zeros((5, t.N), np.uint8))
+    with pytest.raises(bpq.BPQError):
+        bpq.unrolled_loss(t, syn, err, prior, *args, T=T, loss="coset", logicals=np.zeros((0, t.N), np.uint8))

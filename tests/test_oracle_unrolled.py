@@ -120,3 +120,95 @@ def test_momentum_model_gradients_match_finite_differences(case):
         d = np.zeros(g.E); d[e] = h
         assert (f(alpha, beta, w + d, gamma) - f(alpha, beta, w - d, gamma)) / (2 * h) == pytest.approx(
             gw[e], rel=1e-5, abs=1e-9)
+
+
+# ---------------------------------------------------------------- coset loss
+
+
+def brute_force_coset_term(pi, R, target):
+    """-log P(<E^, R> = target) for one operator R by enumerating every
+    assignment of Paulis to its support under the product distribution pi
+    (N, 4) of (I, X, Y, Z)."""
+    import itertools
+    supp = np.nonzero(R)[0]
+    P = 0.0
+    for ops in itertools.product(range(4), repeat=supp.size):
+        pr = np.prod([pi[j, o] for j, o in zip(supp, ops)])
+        par = sum(int(o != 0 and o != R[j]) for j, o in zip(supp, ops)) % 2
+        if par == target:
+            P += pr
+    return -np.log(P)
+
+
+def test_coset_loss_matches_brute_force_enumeration():
+    """Planar d = 3: every check's and logical's parity probability under
+    random posterior marginals equals the sum over all 4^w assignments of
+    its support (the parity convolution is exact), for two iterations."""
+    H, _ = codes.build_code("planar", 3)
+    Lg = codes.logical_operators(H)
+    rng = np.random.default_rng(11)
+    B, N = 2, H.shape[1]
+    err = rng.integers(0, 4, size=(B, N)).astype(np.uint8)
+    syn = codes.syndrome(H, err).astype(np.uint8)
+    Qs = [torch.tensor(rng.normal(2.0, 2.5, size=(B, N, 3))) for _ in range(2)]
+    got = float(unrolled.coset_loss(Qs, H, syn, err, Lg))
+    total = 0.0
+    for Q in Qs:
+        for b in range(B):
+            z = np.concatenate([np.zeros((N, 1)), -Q[b].numpy()], 1)
+            pi = np.exp(z - z.max(1, keepdims=True))
+            pi /= pi.sum(1, keepdims=True)
+            chk = np.mean([brute_force_coset_term(pi, H[i], syn[b, i]) for i in range(H.shape[0])])
+            tl = [int(sum(int(err[b, j] != 0 and Lg[l, j] != 0 and err[b, j] != Lg[l, j]) for j in range(N)) % 2)
+                  for l in range(Lg.shape[0])]
+            log = np.mean([brute_force_coset_term(pi, Lg[l], tl[l]) for l in range(Lg.shape[0])])
+            total += chk + log
+    assert got == pytest.approx(total / (len(Qs) * B), rel=1e-12)
+
+
+def test_coset_loss_vanishes_on_a_certain_correct_posterior():
+    """A posterior concentrated on the true error (or on any error of its
+    coset with the same syndrome) gives P = 1 for every check and logical."""
+    H, _ = codes.build_code("planar", 5)
+    Lg = codes.logical_operators(H)
+    ch = oracle.depolarizing(0.08)
+    err, syn = oracle.sample(H, *ch, seed=5, shot0=0, B=4)
+    B, N = err.shape
+    Q = torch.full((B, N, 3), 60.0, dtype=torch.float64)
+    for b in range(B):
+        for j in range(N):
+            if err[b, j]:
+                Q[b, j, :] = 0.0
+                Q[b, j, err[b, j] - 1] = -60.0
+    assert float(unrolled.coset_loss([Q], H, syn, err, Lg)) < 1e-20
+    # a logical error flips a logical parity: the loss is then large
+    e2 = err.copy()
+    e2[0] = codes.from_symplectic(codes.to_symplectic(err[0]) ^ codes.to_symplectic(Lg[0]))
+    assert float(unrolled.coset_loss([Q[:1]], H, syn[:1], e2[:1], Lg)) > 10.0
+
+
+def test_coset_loss_gradients_match_finite_differences(case):
+    H, err, syn, prior = case
+    Lg = codes.logical_operators(H)
+    T = 5
+    g = unrolled.Graph(H)
+    rng = np.random.default_rng(8)
+    alpha = 0.5 + 0.2 * rng.standard_normal(T)
+    beta = 0.1 * np.abs(rng.standard_normal(T))
+    w = 1.0 + 0.1 * rng.standard_normal(g.E)
+    L, ga, gb, gw = unrolled.loss_and_grads(H, syn[:3], err[:3], prior, alpha, beta, w, T, kind="coset",
+                                            logicals=Lg)
+
+    def f(a, b, ww):
+        Qs = unrolled.forward(g, syn[:3], prior, torch.tensor(a), torch.tensor(b), torch.tensor(ww), T, every=True)
+        return float(unrolled.coset_loss(Qs, H, syn[:3], err[:3], Lg))
+
+    assert f(alpha, beta, w) == pytest.approx(L, rel=1e-12)
+    h = 1e-6
+    for k in [0, 2, T - 1]:
+        d = np.zeros(T); d[k] = h
+        assert (f(alpha + d, beta, w) - f(alpha - d, beta, w)) / (2 * h) == pytest.approx(ga[k], rel=1e-5, abs=1e-9)
+        assert (f(alpha, beta + d, w) - f(alpha, beta - d, w)) / (2 * h) == pytest.approx(gb[k], rel=1e-5, abs=1e-9)
+    for e in [0, 17, g.E - 1]:
+        d = np.zeros(g.E); d[e] = h
+        assert (f(alpha, beta, w + d) - f(alpha, beta, w - d)) / (2 * h) == pytest.approx(gw[e], rel=1e-5, abs=1e-9)
