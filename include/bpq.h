@@ -419,14 +419,20 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
 /* Serve a request trace in real time (host wall clock from the call):
  * request r is decoding code code[r], becomes available at arrival_s[r]
  * seconds (non-decreasing), its packed syndrome is syn_host[syn_off[r] ..
- * + ceil(M/32)), and its outputs go to est_host[est_off[r] .. + N],
- * conv_host[r], iters_host[r].  done_s[r] receives the time at which the
- * host saw the request's lane finish; latency = done_s - arrival_s.
- * lanes_used (may be NULL): the largest number of lanes busy at once.
- * Returns when every request is done. */
+ * + ceil(M/32)), and its outputs go to est_host[est_off[r] .. + N] (within
+ * est_bytes), conv_host[r], iters_host[r].  done_s[r] receives the time at
+ * which the host saw the request finish; latency = done_s - arrival_s.
+ * lanes_used (may be NULL): the largest number of lanes busy at once (slot
+ * server: its CTAs).  Slot server: when est_host, conv_host and iters_host
+ * are page-locked (cudaHostAlloc or cudaHostRegister) and every est_off is a
+ * multiple of 16, the kernel writes each result into them directly and the
+ * host only reads the completion queue; otherwise results pass through the
+ * rings and the host copies them out.  Returns when every request is done.
+ * Errors: EINVAL (NULL arrays, a code index out of range, decreasing
+ * arrival times, an estimate outside est_bytes), ECUDA. */
 int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *arrival_s, const uint32_t *syn_host,
-                      const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, uint8_t *conv_host,
-                      uint8_t *iters_host, double *done_s, int *lanes_used);
+                      const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, size_t est_bytes,
+                      uint8_t *conv_host, uint8_t *iters_host, double *done_s, int *lanes_used);
 
 /* Slot-granular continuous batching (an interface addition; the paper
  * decodes offline batches).  A persistent kernel of resident CTAs decodes
@@ -456,6 +462,11 @@ size_t bpq_server_slot_device_bytes(int n_codes);
  * the CTA's code empty.  Synchronizes.  Errors: EINVAL (not a slot server),
  * ECUDA. */
 int bpq_server_slot_stats(bpq_server *s, long *code_switches, long *empty_scans, long *empty_claims);
+/* The slot server's host loop in its last replay: turns that admitted or
+ * completed something, and the seconds they spent admitting requests and
+ * reading completions (any pointer may be NULL).  Errors: EINVAL (not a
+ * slot server). */
+int bpq_server_host_stats(const bpq_server *s, long *turns, double *admit_s, double *complete_s);
 int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *priors_dev, int n_codes, int variant,
                             const bpq_params *params, int max_iter, int slots_per_code, int idle_timeout_us,
                             void *dev_mem, size_t dev_bytes, bpq_server **out);

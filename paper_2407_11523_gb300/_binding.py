@@ -88,7 +88,9 @@ def lib():
             "bpq_batch_free": (None, [P]),
             "bpq_server_device_bytes": (sz, [P, i, i, i]),
             "bpq_server_create": (i, [P, P, i, i, ctypes.POINTER(Params), i, i, i, P, sz, PP]),
-            "bpq_server_replay": (i, [P, i, P, P, P, P, P, P, P, P, P, pi]),
+            "bpq_server_replay": (i, [P, i, P, P, P, P, P, P, sz, P, P, P, pi]),
+            "bpq_server_host_stats": (i, [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
             "bpq_server_stats": (i, [P, ctypes.POINTER(ctypes.c_long)]),
             "bpq_server_slot_device_bytes": (sz, [i]),
             "bpq_server_slot_stats": (i, [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
@@ -542,10 +544,16 @@ class Server:
         _check(lib().bpq_server_create(harr, parr, n, v, ctypes.byref(self.params), max_iter, n_lanes, max_batch,
                                        _ptr(self.mem), nbytes, ctypes.byref(self._h)), "bpq_server_create")
 
-    def replay(self, code, arrival_s, syn_list):
+    def replay(self, code, arrival_s, syn_list, pinned=None):
         """code: (R,) int; arrival_s: (R,) float, non-decreasing; syn_list:
-        packed syndrome words (uint32 numpy) of each request.  Returns
-        (est list, conv (R,), iters (R,), done_s (R,), lanes_used)."""
+        packed syndrome words (uint32 numpy) of each request.  pinned: the
+        outputs live in page-locked memory at 16-byte aligned offsets, so the
+        slot server writes them directly (else through its rings); default:
+        for the slot server only (the lane server's host copies run faster
+        into pageable memory).  Returns (est list, conv (R,), iters (R,),
+        done_s (R,), lanes_used)."""
+        if pinned is None:
+            pinned = self.mode == "slots"
         code = np.ascontiguousarray(code, dtype=np.int32)
         arrival = np.ascontiguousarray(arrival_s, dtype=np.float64)
         R = code.size
@@ -554,15 +562,22 @@ class Server:
         Ns = [self.codes[c].N for c in code]
         lens = [len(x) for x in syn_list]
         syn_off[1:] = np.cumsum(lens)[:-1]
-        est_off[1:] = np.cumsum(Ns)[:-1]
+        stride = [(n + 15) & ~15 for n in Ns] if pinned else Ns
+        est_off[1:] = np.cumsum(stride)[:-1]
         syn = np.ascontiguousarray(np.concatenate(syn_list).astype(np.uint32)) if R else np.zeros(1, np.uint32)
-        est = np.zeros(max(1, int(sum(Ns))), dtype=np.uint8)
-        conv = np.zeros(max(1, R), dtype=np.uint8)
-        iters = np.zeros(max(1, R), dtype=np.uint8)
+        n_est = max(16, int(sum(stride)))
+
+        def buf(n):
+            if pinned:
+                return torch.zeros(n, dtype=torch.uint8, pin_memory=True).numpy()
+            return np.zeros(n, dtype=np.uint8)
+
+        est, conv, iters = buf(n_est), buf(max(1, R)), buf(max(1, R))
         done = np.zeros(max(1, R), dtype=np.float64)
         used = ctypes.c_int()
         _check(lib().bpq_server_replay(self._h, R, _ptr(code), _ptr(arrival), _ptr(syn), _ptr(syn_off), _ptr(est),
-                                       _ptr(est_off), _ptr(conv), _ptr(iters), _ptr(done), ctypes.byref(used)),
+                                       _ptr(est_off), n_est, _ptr(conv), _ptr(iters), _ptr(done),
+                                       ctypes.byref(used)),
                "bpq_server_replay")
         ests = [est[o:o + n] for o, n in zip(est_off, Ns)]
         return ests, conv[:R], iters[:R], done[:R], used.value
@@ -574,6 +589,14 @@ class Server:
         _check(lib().bpq_server_slot_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
                "bpq_server_slot_stats")
         return a.value, b.value, c.value
+
+    def host_stats(self):
+        """Slot server host loop of the last replay: (turns with work, seconds
+        admitting, seconds reading completions)."""
+        n, a, c = ctypes.c_long(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().bpq_server_host_stats(self._h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(c)),
+               "bpq_server_host_stats")
+        return n.value, a.value, c.value
 
     def launches(self):
         """Decode kernels launched since creation."""

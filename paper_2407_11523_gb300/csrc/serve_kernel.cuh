@@ -24,6 +24,13 @@
 
 namespace bpq {
 
+// Output buffers of a request stream that the kernel writes directly: the
+// caller's device-accessible (pinned) host buffers; est == nullptr: results
+// go to the rings and the host copies them out.
+struct ServeOut {
+    uint8_t *est, *conv, *iters;
+};
+
 struct ServeArgs {
     const DecodeArgs *codes;   // per code: syn/est point at the code's rings (est slots padded to 16
                                // bytes), B = ring slots
@@ -32,14 +39,18 @@ struct ServeArgs {
     uint32_t *head;            // [ncodes] claimed requests (device)
     const uint32_t *closed;    // host-mapped: 1 once every request has been published
     uint32_t *cq_count;        // device: completions so far
-    uint4 *cq;                 // host-mapped completion queue [cq_len]: {e + 1, code, request number,
-                               //  converged | iterations << 8}
+    uint4 *cq;                 // host-mapped completion queue [cq_len]: {e + 1, code, request number
+                               //  (direct mode: the caller's request index), converged | iterations << 8}
     uint32_t cq_len;
     uint32_t *status;          // device: [1] error word (as bpq_decode's), [2] exit reason,
                                // [3] code switches, [4] empty scans, [5] claims that found nothing
     uint32_t idle_limit;       // empty scans before the kernel returns
     uint32_t stage_offset;     // byte offset of the staging area in dynamic shared memory
     int ncodes;
+    const ServeOut *out;       // device: the caller's output buffers of this stream (est null: the rings)
+    const uint4 *dst;          // host-mapped [ncodes][cap]: per slot {estimate offset (lo, hi), request, 0}
+    uint32_t *consumed;        // host-mapped [ncodes][cap] (direct mode): request number + 1 whose syndrome
+                               // the kernel has staged from the slot, which the host may then reuse
 };
 
 // Per-CTA staging of the requests in flight, after the code's group memory:
@@ -84,6 +95,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_serve_kernel(const Se
     // the CTA's batch of claimed requests of its current code: [cl_base,
     // cl_base + cl_cnt), refilled under cl_lock
     __shared__ int cl_lock, cl_base, cl_cnt;
+    // each group's output offset and request number (direct mode), fetched
+    // from host memory with the syndrome
+    __shared__ uint4 grp_dst[kMaxGroupsPerCta];
     if (tid == 0) cl_lock = cl_base = cl_cnt = 0;
     int cur = -1;
     int from = (int)(blockIdx.x % (unsigned)s.ncodes);
@@ -270,7 +284,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_serve_kernel(const Se
                 // (ld.global.cv: the slot is rewritten by the host between uses)
                 uint32_t *ssyn = const_cast<uint32_t *>(a.syn) + (size_t)group * a.W;
                 for (int w = tg; w < a.W; w += T) ssyn[w] = __ldcv(ring_syn + (size_t)slot * a.W + w);
+                if (tg == T - 1 && s.out->est) grp_dst[group] = __ldcv(s.dst + (size_t)g * cap + slot);
                 group_sync(G, bar_id);
+                // direct mode: the slot's syndrome and destination are in shared
+                // memory now (read before the barrier), so the slot is free for
+                // the next request even while this one decodes
+                if (tg == 0 && s.out->est) st_release_sys(s.consumed + (size_t)g * cap + slot, (uint32_t)k + 1u);
                 if (a.split)
                     decode_shot<VARIANT, NPT, false, true, false, true>(a, adj, m, a.npt, T, tg, G, bar_id, group,
                                                                          a.alpha);
@@ -279,15 +298,29 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_serve_kernel(const Se
                                                                           a.alpha);
                 group_sync(G, bar_id);
                 // warp 0 alone writes to host memory: the estimate (decode_shot
-                // wrote it at est + group * N) to the ring slot (stride N rounded
-                // up to 16) in 16-byte stores, then the completion, which carries
-                // the converged flag and iteration count (the host reads one line
-                // per request besides the estimate)
+                // wrote it at est + group * N) in 16-byte stores, to the request's
+                // own output (direct mode: the offset the host left in the slot,
+                // 16-byte aligned; the last partial chunk byte by byte) or to the
+                // ring slot (stride N rounded up to 16), then the completion, which
+                // carries the converged flag and iteration count
                 if (tg < 32) {
                     const size_t n16 = ((size_t)a.N + 15) & ~size_t(15);
                     const uint8_t *se = a.est + (size_t)group * a.N;
-                    uint4 *de = reinterpret_cast<uint4 *>(ring_est + (size_t)slot * n16);
-                    for (int v = tg; v < (int)(n16 / 16); v += 32) {
+                    uint8_t *const out_est = s.out->est;
+                    uint8_t *dbase = ring_est + (size_t)slot * n16;
+                    int full = (int)(n16 / 16);
+                    if (out_est) {
+                        const uint4 dm = grp_dst[group];
+                        dbase = out_est + ((uint64_t)dm.x | ((uint64_t)dm.y << 32));
+                        full = a.N / 16;
+                        if (tg == 0) {
+                            s.out->conv[dm.z] = a.conv[group];
+                            s.out->iters[dm.z] = a.iters[group];
+                        }
+                        for (int j = 16 * full + tg; j < a.N; j += 32) dbase[j] = se[j];
+                    }
+                    uint4 *de = reinterpret_cast<uint4 *>(dbase);
+                    for (int v = tg; v < full; v += 32) {
                         uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
                         for (int b = 0; b < 16; ++b) {
@@ -304,7 +337,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_serve_kernel(const Se
                         const uint32_t e = atomicAdd(s.cq_count, 1u);
                         uint4 *q = s.cq + (e % s.cq_len);
                         q->y = (uint32_t)g;
-                        q->z = (uint32_t)k;
+                        q->z = out_est ? grp_dst[group].z : (uint32_t)k;  // direct: the request itself
                         q->w = (uint32_t)a.conv[group] | ((uint32_t)a.iters[group] << 8);
                         __threadfence_system();
                         st_release_sys(&q->x, e + 1u);

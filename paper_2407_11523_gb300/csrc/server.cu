@@ -77,6 +77,9 @@ struct SlotRings {
     uint8_t *host = nullptr;           // one mapped pinned allocation
     uint32_t *tail = nullptr, *closed = nullptr;
     uint4 *cq = nullptr;
+    uint4 *dst = nullptr;              // [n_codes][cap]: each slot's output offset and request (direct mode)
+    uint32_t *consumed = nullptr;      // [n_codes][cap]: request number + 1 staged from the slot (direct mode)
+    bpq::ServeOut *out_dev = nullptr;  // device: the output buffers of the current stream
     std::vector<uint32_t *> syn;       // per code [cap][W]
     std::vector<uint8_t *> est, conv, iters;  // per code [cap][N], [cap], [cap]
     // device
@@ -90,6 +93,10 @@ struct SlotRings {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t stage_offset = 0, stage_bytes = 0;  // staging area in the kernel's shared memory
+    // host loop of the last replay: turns with work, seconds spent admitting
+    // requests and reading completions
+    long turns = 0;
+    double admit_s = 0.0, complete_s = 0.0;
 };
 
 struct bpq_server {
@@ -148,7 +155,21 @@ void free_server(bpq_server *s) {
 namespace {
 
 size_t slot_device_bytes(int n_codes) {
-    return a256(sizeof(bpq::DecodeArgs) * (size_t)n_codes) + 2 * a256(sizeof(uint32_t) * (size_t)n_codes) + 256;
+    return a256(sizeof(bpq::DecodeArgs) * (size_t)n_codes) + 2 * a256(sizeof(uint32_t) * (size_t)n_codes) + 512;
+}
+
+// Device pointer of a host buffer of `bytes` bytes if both its ends lie in
+// page-locked (pinned or registered) host memory, else nullptr.
+uint8_t *pinned_device_pointer(const void *p, size_t bytes) {
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a0{}, a1{};
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess ||
+        cudaPointerGetAttributes(&a1, static_cast<const uint8_t *>(p) + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();  // pageable memory may report an error on older drivers
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer) return nullptr;
+    return static_cast<uint8_t *>(a0.devicePointer);
 }
 
 using steady = std::chrono::steady_clock;
@@ -170,19 +191,36 @@ int slot_launch(bpq_server *s) {
 }
 
 int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival_s, const uint32_t *syn_host,
-                const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, uint8_t *conv_host,
-                uint8_t *iters_host, double *done_s, int *lanes_used) {
+                const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, size_t est_bytes,
+                uint8_t *conv_host, uint8_t *iters_host, double *done_s, int *lanes_used) {
     SlotRings &R = s->ring;
     const int n_codes = (int)s->codes.size(), cap = R.cap;
+    // direct mode: with page-locked outputs and 16-byte aligned estimate
+    // offsets the kernel writes every result where it belongs, and the host
+    // only reads the completion queue; otherwise results go through the rings
+    bpq::ServeOut out{nullptr, nullptr, nullptr};
+    bool aligned = n_req > 0;
+    for (int r = 0; r < n_req && aligned; ++r) aligned = (est_off[r] & 15) == 0;
+    if (aligned) {
+        out.est = pinned_device_pointer(est_host, est_bytes);
+        out.conv = pinned_device_pointer(conv_host, (size_t)n_req);
+        out.iters = pinned_device_pointer(iters_host, (size_t)n_req);
+        if (!out.est || !out.conv || !out.iters) out = bpq::ServeOut{nullptr, nullptr, nullptr};
+    }
+    const bool direct = out.est != nullptr;
     // a fresh stream of requests: claim counters, completion count, counters,
     // tails and queue
     int rc = bpq::cuda_check(cudaMemsetAsync(R.head, 0, sizeof(uint32_t) * n_codes, R.st), "server reset");
     if (!rc) rc = bpq::cuda_check(cudaMemsetAsync(R.status, 0, 6 * sizeof(uint32_t), R.st), "server reset");
     if (!rc) rc = bpq::cuda_check(cudaMemsetAsync(R.cq_count, 0, sizeof(uint32_t), R.st), "server reset");
+    if (!rc)
+        rc = bpq::cuda_check(cudaMemcpyAsync(R.out_dev, &out, sizeof out, cudaMemcpyHostToDevice, R.st),
+                             "server outputs");
     if (!rc) rc = bpq::cuda_check(cudaStreamSynchronize(R.st), "server reset");
     if (rc) return rc;
     for (int c = 0; c < n_codes; ++c) __atomic_store_n(R.tail + c, 0u, __ATOMIC_RELAXED);
     std::memset(R.cq, 0, sizeof(uint4) * R.cq_len);
+    std::memset(R.consumed, 0, sizeof(uint32_t) * (size_t)n_codes * cap);
     __atomic_store_n(R.closed, 0u, __ATOMIC_RELEASE);
     if (lanes_used) *lanes_used = 0;
     if (n_req == 0) return BPQ_OK;
@@ -206,18 +244,23 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
     // freed by a completion), so each turn of the loop costs only its work
     std::vector<std::vector<int>> pend(n_codes);
     std::vector<size_t> pend_head(n_codes, 0);
-    std::vector<int> work;
+    std::vector<int> work, blocked;
     std::vector<char> queued(n_codes, 0);
     work.reserve(n_codes);
-    constexpr int kCompletionsPerTurn = 256;
+    blocked.reserve(n_codes);
+    uint32_t admitted_total = 0;
+    constexpr int kCompletionsPerTurn = 256, kArrivalsPerTurn = 1024;
     int next = 0, completed = 0;
     uint32_t cq_read = 0;
+    R.turns = 0;
+    R.admit_s = R.complete_s = 0.0;
     while (completed < n_req) {
         const int next0 = next, completed0 = completed;
         bool admitted_any = false;
-        // requests that have arrived join their code's FIFO
+        // requests that have arrived join their code's FIFO, a bounded number
+        // per turn, so that a burst does not hold back the first admissions
         const double tnow = now();
-        while (next < n_req && arrival_s[next] <= tnow) {
+        for (int n = 0; n < kArrivalsPerTurn && next < n_req && arrival_s[next] <= tnow; ++n) {
             const int c = code[next];
             pend[c].push_back(next);
             if (!queued[c]) {
@@ -234,13 +277,39 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
             size_t &h = pend_head[c];
             bool any = false;
             while (h < P.size()) {
-                const int slot = (int)(admitted[c] % (uint32_t)cap);
+                // every admitted request that has not completed may still
+                // write a completion, so at most cq_len - 1 of them: the queue
+                // never overwrites an entry the host has not read.  (Ring mode
+                // keeps this by itself: a slot is refilled only after its
+                // completion has been read, and cq_len = codes x slots + 1.)
+                if (admitted_total - (uint32_t)completed >= R.cq_len - 1u) {
+                    if (!queued[c]) {
+                        queued[c] = 1;
+                        blocked.push_back(c);
+                    }
+                    break;
+                }
+                const uint32_t k = admitted[c];
+                const int slot = (int)(k % (uint32_t)cap);
                 int &occ = req_of[(size_t)c * cap + slot];
-                if (occ >= 0) break;  // ring full: a completion relists the code
+                if (direct) {
+                    // the slot is free once the kernel has staged the request
+                    // that used it (number k - cap), even while that request
+                    // still decodes
+                    if (k >= (uint32_t)cap &&
+                        __atomic_load_n(R.consumed + (size_t)c * cap + slot, __ATOMIC_ACQUIRE) != k - cap + 1u)
+                        break;  // a completion relists the code
+                } else if (occ >= 0) {
+                    break;  // ring full: a completion relists the code
+                }
                 const int r = P[h++];
                 std::memcpy(R.syn[c] + (size_t)slot * W[c], syn_host + syn_off[r], sizeof(uint32_t) * W[c]);
+                if (direct)
+                    R.dst[(size_t)c * cap + slot] = make_uint4((uint32_t)est_off[r], (uint32_t)(est_off[r] >> 32),
+                                                               (uint32_t)r, 0u);
                 occ = r;
                 ++admitted[c];
+                ++admitted_total;
                 any = true;
             }
             if (any) {
@@ -249,6 +318,9 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
             }
         }
         work.clear();
+        // codes held back by the completion queue's bound try again next turn
+        work.swap(blocked);
+        const double tadm = now();
         // completions, in the order the kernel wrote them, a bounded number per
         // turn so that freed slots are refilled promptly; one clock read per turn
         double tdone = -1.0;
@@ -260,15 +332,22 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
             const int c = (int)q->y;
             const uint32_t k = q->z, cw = q->w;
             if (c < 0 || c >= n_codes) return fail(BPQ_ECUDA, "server: completion of an unknown code");
-            const int slot = (int)(k % (uint32_t)cap);
-            int &occ = req_of[(size_t)c * cap + slot];
-            const int r = occ;
-            if (r < 0) return fail(BPQ_ECUDA, "server: completion of a request that is not in flight");
-            std::memcpy(est_host + est_off[r], R.est[c] + (size_t)slot * N16[c], N[c]);
-            conv_host[r] = (uint8_t)(cw & 0xFFu);
-            iters_host[r] = (uint8_t)((cw >> 8) & 0xFFu);
+            int r;
+            if (direct) {
+                // the entry names the request; its outputs are in place
+                r = (int)k;
+                if (r < 0 || r >= n_req) return fail(BPQ_ECUDA, "server: completion of an unknown request");
+            } else {
+                const int slot = (int)(k % (uint32_t)cap);
+                int &occ = req_of[(size_t)c * cap + slot];
+                r = occ;
+                if (r < 0) return fail(BPQ_ECUDA, "server: completion of a request that is not in flight");
+                std::memcpy(est_host + est_off[r], R.est[c] + (size_t)slot * N16[c], N[c]);
+                conv_host[r] = (uint8_t)(cw & 0xFFu);
+                iters_host[r] = (uint8_t)((cw >> 8) & 0xFFu);
+                occ = -1;
+            }
             done_s[r] = tdone;
-            occ = -1;
             if (!queued[c] && pend_head[c] < pend[c].size()) {
                 queued[c] = 1;
                 work.push_back(c);
@@ -276,10 +355,16 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
             ++completed;
             ++cq_read;
         }
+        if (next != next0 || completed != completed0 || admitted_any) {
+            const double tend = now();
+            ++R.turns;
+            R.admit_s += tadm - tnow;
+            R.complete_s += tend - tadm;
+            continue;
+        }
         // the kernel returns after an idle period (or a device error): read its
         // status and relaunch it while requests remain (checked on the host
         // loop's idle turns only; the query is a driver call)
-        if (next != next0 || completed != completed0 || admitted_any) continue;
         const cudaError_t q = cudaEventQuery(R.exited);
         if (q == cudaSuccess && completed < n_req) {
             uint32_t st3[3];
@@ -420,8 +505,8 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
 }
 
 int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *arrival_s, const uint32_t *syn_host,
-                      const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, uint8_t *conv_host,
-                      uint8_t *iters_host, double *done_s, int *lanes_used) {
+                      const int64_t *syn_off, uint8_t *est_host, const int64_t *est_off, size_t est_bytes,
+                      uint8_t *conv_host, uint8_t *iters_host, double *done_s, int *lanes_used) {
     if (!s) return fail(BPQ_EINVAL, "server is NULL");
     if (n_req < 0 || (n_req > 0 && (!code || !arrival_s || !syn_host || !syn_off || !est_host || !est_off ||
                                     !conv_host || !iters_host || !done_s)))
@@ -430,12 +515,14 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
     for (int r = 0; r < n_req; ++r) {
         if (code[r] < 0 || code[r] >= n_codes) return fail(BPQ_EINVAL, "request code index out of range");
         if (r > 0 && arrival_s[r] < arrival_s[r - 1]) return fail(BPQ_EINVAL, "arrival times must not decrease");
+        if (est_off[r] < 0 || (size_t)est_off[r] + (size_t)s->codes[code[r]]->N > est_bytes)
+            return fail(BPQ_EINVAL, "a request's estimate lies outside est_host");
     }
     int rc = bpq::cuda_set_device(s->device);
     if (rc) return rc;
     if (s->slots)
-        return slot_replay(s, n_req, code, arrival_s, syn_host, syn_off, est_host, est_off, conv_host, iters_host,
-                           done_s, lanes_used);
+        return slot_replay(s, n_req, code, arrival_s, syn_host, syn_off, est_host, est_off, est_bytes, conv_host,
+                           iters_host, done_s, lanes_used);
     using clock = std::chrono::steady_clock;
     const auto t0 = clock::now();
     auto now = [&]() { return std::chrono::duration<double>(clock::now() - t0).count(); };
@@ -550,6 +637,14 @@ int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *a
 
 size_t bpq_server_slot_device_bytes(int n_codes) { return n_codes < 1 ? 0 : slot_device_bytes(n_codes); }
 
+int bpq_server_host_stats(const bpq_server *s, long *turns, double *admit_s, double *complete_s) {
+    if (!s || !s->slots) return fail(BPQ_EINVAL, "not a slot server");
+    if (turns) *turns = s->ring.turns;
+    if (admit_s) *admit_s = s->ring.admit_s;
+    if (complete_s) *complete_s = s->ring.complete_s;
+    return BPQ_OK;
+}
+
 int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *priors_dev, int n_codes, int variant,
                             const bpq_params *params, int max_iter, int slots_per_code, int idle_timeout_us,
                             void *dev_mem, size_t dev_bytes, bpq_server **out) {
@@ -614,6 +709,10 @@ int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *
     R.cq_len = (uint32_t)std::min<size_t>((size_t)n_codes * slots_per_code + 1, size_t(1) << 31);
     const size_t o_cq = total;
     total += a256(sizeof(uint4) * R.cq_len);
+    const size_t o_dst = total;
+    total += a256(sizeof(uint4) * (size_t)n_codes * slots_per_code);
+    const size_t o_consumed = total;
+    total += a256(sizeof(uint32_t) * (size_t)n_codes * slots_per_code);
     for (int c = 0; c < (int)s->codes.size(); ++c) {
         const size_t W = (s->codes[c]->M + 31) / 32, N16 = ((size_t)s->codes[c]->N + 15) & ~size_t(15);
         o_syn[c] = total;
@@ -635,6 +734,8 @@ int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *
         R.tail = reinterpret_cast<uint32_t *>(R.host + o_tail);
         R.closed = reinterpret_cast<uint32_t *>(R.host + o_closed);
         R.cq = reinterpret_cast<uint4 *>(R.host + o_cq);
+        R.dst = reinterpret_cast<uint4 *>(R.host + o_dst);
+        R.consumed = reinterpret_cast<uint32_t *>(R.host + o_consumed);
         for (int c = 0; c < n_codes; ++c) {
             R.syn.push_back(reinterpret_cast<uint32_t *>(R.host + o_syn[c]));
             R.est.push_back(R.host + o_est[c]);
@@ -656,13 +757,15 @@ int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *
         p += a256(sizeof(uint32_t) * n_codes);
         R.cq_count = reinterpret_cast<uint32_t *>(p);
         R.status = R.cq_count + 4;
+        p += 256;
+        R.out_dev = reinterpret_cast<bpq::ServeOut *>(p);
         std::vector<uint32_t> caps(n_codes, (uint32_t)slots_per_code);
         rc = bpq::cuda_check(cudaMemcpy(R.desc, s->tmpl.data(), sizeof(bpq::DecodeArgs) * n_codes,
                                         cudaMemcpyHostToDevice), "server descriptors");
         if (!rc)
             rc = bpq::cuda_check(cudaMemcpy(R.cap_dev, caps.data(), sizeof(uint32_t) * n_codes, cudaMemcpyHostToDevice),
                                  "server descriptors");
-        if (!rc) rc = bpq::cuda_check(cudaMemset(R.cq_count, 0, 256), "server descriptors");
+        if (!rc) rc = bpq::cuda_check(cudaMemset(R.cq_count, 0, 512), "server descriptors");  // and out_dev
     }
     if (!rc) {
         R.fn = bpq::pick_serve_kernel(variant);
@@ -690,6 +793,9 @@ int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *
         args.idle_limit = R.idle_limit;
         args.stage_offset = (uint32_t)R.stage_offset;
         args.ncodes = n_codes;
+        args.out = R.out_dev;
+        args.dst = reinterpret_cast<const uint4 *>(dev_host + o_dst);
+        args.consumed = reinterpret_cast<uint32_t *>(dev_host + o_consumed);
         cudaError_t e = cudaStreamBeginCapture(R.st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaMemsetAsync(R.status, 0, 3 * sizeof(uint32_t), R.st);  // error word and exit reason

@@ -96,6 +96,25 @@ def test_slot_server_results_equal_alone(bpq, rate, slots):
     check_alone(bpq, codes, priors, code_of, syn_list, ests, conv, iters)
 
 
+def test_slot_server_direct_and_ring_outputs_agree(bpq):
+    """Page-locked outputs at 16-byte aligned offsets (the kernel writes each
+    result in place) and pageable outputs (results through the rings, copied
+    by the host) give the same results, equal to decoding alone; planar
+    d = 17 and 9 have N = 545 and 145, so estimates end in a partial
+    16-byte chunk."""
+    codes = [bpq.Tanner("planar", 17), bpq.Tanner("xzzx", 5), bpq.Tanner("planar", 9)]
+    ch = oracle.depolarizing(0.05)
+    priors = [bpq.prior_tensor(t, *ch) for t in codes]
+    srv = bpq.Server(codes, priors, "ewainit", max_iter=100, mode="slots", slots_per_code=32)
+    code_of, arrival, syn_list = make_trace(bpq, codes, 1500, 2e5, seed=35)
+    direct = srv.replay(code_of, arrival, syn_list, pinned=True)
+    ring = srv.replay(code_of, arrival, syn_list, pinned=False)
+    for r in range(code_of.size):
+        assert (direct[0][r] == ring[0][r]).all()
+    assert (direct[1] == ring[1]).all() and (direct[2] == ring[2]).all()
+    check_alone(bpq, codes, priors, code_of, syn_list, *direct[:3])
+
+
 def test_slot_server_relaunches_after_idle(bpq):
     """With a 50 us idle limit and 3 ms gaps between bursts, the serving
     kernel returns (a bounded wait, status 2) between bursts and the host
