@@ -100,7 +100,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_serve_kernel(const Se
     __shared__ uint4 grp_dst[kMaxGroupsPerCta];
     if (tid == 0) cl_lock = cl_base = cl_cnt = 0;
     int cur = -1;
-    int from = (int)(blockIdx.x % (unsigned)s.ncodes);
+    // the CTA's home code: every scan for a code with requests starts there,
+    // so that the CTAs spread over the codes with requests instead of all
+    // taking the first one published and then moving through the codes in
+    // the same order
+    const int from = (int)(blockIdx.x % (unsigned)s.ncodes);
     uint32_t phase = 0, idle = 0;
     ThreadAdj<NPT> adj;
     for (;;) {
@@ -143,7 +147,6 @@ __global__ void __launch_bounds__(kBatchThreads, 1) decode_serve_kernel(const Se
             }
             continue;
         }
-        from = g;
         if (g != cur) {
             if (tid == 0) atomicAdd(s.status + 3, 1u);
             // switch code: descriptor, adjacency (bulk TMA), prior, zero slots; the
