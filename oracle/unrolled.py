@@ -206,7 +206,7 @@ def loss_and_grads(H, syn, err, prior, alpha, beta, w, T: int, clip: float = 30.
     else:
         L = loss(forward(g, syn, prior, a, b, ww, T, clip, model=model, gamma=gm), err)
     L.backward()
-    out = (float(L), a.grad.numpy(), b.grad.numpy(), ww.grad.numpy())
+    out = (L.item(), a.grad.numpy(), b.grad.numpy(), ww.grad.numpy())
     if model == "momentum":
         out = out + (gm.grad.numpy(),)
     return out
