@@ -178,9 +178,11 @@ int bpq_decode_status(const void *work_dev, void *stream, int *device_error);
  * caller-owned device memory of at least bpq_decode_host_bytes(t, B) bytes.
  * Host buffers should be pinned for the copies to run asynchronously.  From
  * B >= 131072 the batch is cut into up to 8 chunks whose host-to-device
- * copies, decodes (on `stream`) and device-to-host copies overlap; the copies
- * run on two library-owned streams per device, created on first use and
- * kept (calls from several host threads on one device share them). */
+ * copies, decodes and device-to-host copies overlap; the chunks decode
+ * alternately on `stream` and on a library stream (so that one chunk's last
+ * shots overlap the next chunk), and the copies run on two more library
+ * streams, all three per device, created on first use and kept (calls from
+ * several host threads on one device share them). */
 size_t bpq_decode_host_bytes(const bpq_tanner *t, int B);
 int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host,
                     int variant, const bpq_params *params, int max_iter, int B, uint8_t *est_host,

@@ -270,7 +270,7 @@ int cuda_set_device(int device) {
 // Copy streams of one device for the pipelined host path (created on first
 // use, kept for the life of the process).
 struct HostPipe {
-    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr, comp = nullptr;
 };
 std::mutex g_pipe_mu;
 HostPipe g_pipe[64];
@@ -284,6 +284,8 @@ int host_pipe(int device, HostPipe **out) {
         if (rc) return rc;
         rc = cuda_check(cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking), "copy stream");
         if (rc) return rc;
+        rc = cuda_check(cudaStreamCreateWithFlags(&hp.comp, cudaStreamNonBlocking), "decode stream");
+        if (rc) return rc;
     }
     *out = &hp;
     return BPQ_OK;
@@ -291,9 +293,12 @@ int host_pipe(int device, HostPipe **out) {
 
 // bpq_decode_host.  With `pipelined`, batches of at least 2 x kChunkShots
 // shots are cut into up to kMaxChunks chunks whose host-to-device copies
-// (one copy stream), decodes (the caller's stream) and device-to-host copies
-// (a second copy stream) overlap, ordered by events; without it (the
-// no-allocation path) everything runs on the caller's stream in order.
+// (one copy stream), decodes and device-to-host copies (a second copy
+// stream) overlap, ordered by events.  Consecutive chunks decode on two
+// streams (the caller's and a library stream, each with its own workspace),
+// so that a chunk's CTAs take the SMs that the previous chunk's last, slowest
+// shots leave free.  Without `pipelined` (the no-allocation path) everything
+// runs on the caller's stream in order.
 int decode_host_impl(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host, int variant,
                      const bpq_params *params, int max_iter, int B, uint8_t *est_host, uint8_t *conv_host,
                      uint8_t *iters_host, void *dev_buf, size_t dev_buf_bytes, void *stream, bool pipelined) {
@@ -309,6 +314,8 @@ int decode_host_impl(const bpq_tanner *t, const uint32_t *syn_host, const float 
     const size_t W = (t->M + 31) / 32, N = (size_t)t->N;
     uint8_t *p = static_cast<uint8_t *>(dev_buf);
     void *work = p;
+    p += al(kWorkspaceBytes);
+    void *work2 = p;  // the second decode stream's workspace
     p += al(kWorkspaceBytes);
     uint32_t *syn = reinterpret_cast<uint32_t *>(p);
     p += al(sizeof(uint32_t) * W * B);
@@ -350,14 +357,15 @@ int decode_host_impl(const bpq_tanner *t, const uint32_t *syn_host, const float 
     }
     for (int c = 0; c < chunks && !rc; ++c) {
         const int b0 = (int)((long)B * c / chunks), nb = (int)((long)B * (c + 1) / chunks) - b0;
+        cudaStream_t cs = (c & 1) ? hp->comp : st;
         rc = cuda_check(cudaMemcpyAsync(syn + W * b0, syn_host + W * b0, sizeof(uint32_t) * W * nb,
                                         cudaMemcpyHostToDevice, hp->h2d), "H2D");
         if (!rc) rc = cuda_check(cudaEventRecord(ev[2 * c], hp->h2d), "event");
-        if (!rc) rc = cuda_check(cudaStreamWaitEvent(st, ev[2 * c], 0), "wait");
+        if (!rc) rc = cuda_check(cudaStreamWaitEvent(cs, ev[2 * c], 0), "wait");
         if (!rc)
             rc = bpq_decode(t, syn + W * b0, prior, variant, params, max_iter, nb, est + N * b0, conv + b0,
-                            iters + b0, work, stream);
-        if (!rc) rc = cuda_check(cudaEventRecord(ev[2 * c + 1], st), "event");
+                            iters + b0, (c & 1) ? work2 : work, cs);
+        if (!rc) rc = cuda_check(cudaEventRecord(ev[2 * c + 1], cs), "event");
         if (!rc) rc = cuda_check(cudaStreamWaitEvent(hp->d2h, ev[2 * c + 1], 0), "wait");
         if (!rc)
             rc = cuda_check(cudaMemcpyAsync(est_host + N * b0, est + N * b0, N * nb, cudaMemcpyDeviceToHost, hp->d2h),
@@ -369,9 +377,10 @@ int decode_host_impl(const bpq_tanner *t, const uint32_t *syn_host, const float 
     // drain everything that was queued, also after an error
     const int rc_d2h = cuda_check(cudaStreamSynchronize(hp->d2h), "stream sync");
     const int rc_h2d = cuda_check(cudaStreamSynchronize(hp->h2d), "stream sync");
+    const int rc_cp = cuda_check(cudaStreamSynchronize(hp->comp), "stream sync");
     const int rc_st = cuda_check(cudaStreamSynchronize(st), "stream sync");
     for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
-    return rc ? rc : rc_d2h ? rc_d2h : rc_h2d ? rc_h2d : rc_st;
+    return rc ? rc : rc_d2h ? rc_d2h : rc_h2d ? rc_h2d : rc_cp ? rc_cp : rc_st;
 }
 
 }  // namespace bpq
@@ -498,7 +507,7 @@ size_t bpq_decode_host_bytes(const bpq_tanner *t, int B) {
     if (!t || B < 0) return 0;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t W = (t->M + 31) / 32;
-    return al(bpq::kWorkspaceBytes) + al(sizeof(uint32_t) * W * B) + al(sizeof(float) * 3 * t->N) +
+    return 2 * al(bpq::kWorkspaceBytes) + al(sizeof(uint32_t) * W * B) + al(sizeof(float) * 3 * t->N) +
            al((size_t)B * t->N) + al(B) + al(B);
 }
 
