@@ -850,7 +850,8 @@ def run_serve(args, rank, world):
                                        "arrivals; value = the slot server's saturation shots/s (200000 requests "
                                        "available at once)",
                            "slot_server": "1024 request slots per code in mapped host memory, one persistent "
-                                          "kernel (bpq_server_create_slots)",
+                                          "kernel (bpq_server_create_slots); results written in place to "
+                                          "page-locked outputs",
                            "lane_server": "4 lanes x 4096 shots of device budget, one batched launch per dispatch "
                                           "(bpq_server_create)",
                            "servers": out},
