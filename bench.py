@@ -839,6 +839,34 @@ def run_serve(args, rank, world):
         out[name] = {"loads": results, "saturation_shots_per_s": sat,
                      "launches": srv.launches() - launches0}
         launches += srv.launches() - launches0
+    # the device's own rate on the burst's requests: one batched launch over
+    # their syndromes, grouped by code and resident on the device (no host
+    # loop, no rings); an L2 flush runs between timed launches
+    dev = torch.device("cuda")
+    items = []
+    for c, t in enumerate(codes):
+        n = int((code_pool == c).sum())
+        if n:
+            items.append((t, torch.from_numpy(np.ascontiguousarray(pool[c][:n]).view(np.int32)).to(dev), priors[c]))
+    plan = bpq.BatchPlan(items, "ewainit", params=params, max_iter=MAX_ITER)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        plan.run()
+    torch.cuda.synchronize()
+    dev_ms = []
+    for s_ in range(5):
+        flush.fill_(s_ & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.run()
+        e1.record()
+        e1.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+    dev_s = reduce_max(statistics.median(dev_ms) / 1e3, world)
+    device_rate = R_pool / dev_s
+    out["device_batched"] = {"requests": R_pool, "ms": dev_s * 1e3, "shots_per_s": device_rate, "launches": 5}
+    for name in ("slots", "lanes"):
+        out[name]["saturation_of_device_batched"] = out[name]["saturation_shots_per_s"] / device_rate
     if rank == 0:
         best = out["slots"]["saturation_shots_per_s"]
         line = {"metric": "serving: p50/p99 latency and shots/s under a Poisson request stream (continuous batching)",
@@ -854,6 +882,9 @@ def run_serve(args, rank, world):
                                           "page-locked outputs",
                            "lane_server": "4 lanes x 4096 shots of device budget, one batched launch per dispatch "
                                           "(bpq_server_create)",
+                           "device_batched": "the saturation burst's 200000 requests decoded by one batched launch "
+                                             "from device-resident syndromes grouped by code (CUDA events, L2 "
+                                             "flush between launches): the device's rate with no serving work",
                            "servers": out},
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)
