@@ -462,15 +462,18 @@ __global__ void train_backward_kernel(const TrainArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int Np = a.n_pad, K = a.K, S4 = 4 * Np + 4;
     const bool coset = a.loss_kind == kCoset;
-    float2 *ub2 = reinterpret_cast<float2 *>(sm);   // [S4] (coset loss only)
-    float *Pi0 = sm + (coset ? 2 * S4 : 0);          // [3Np]
+    float *Pi0 = sm;                                 // [3Np]
     float *vh = Pi0 + 3 * Np;                        // [(K+1)][S4]   m_v->c^(t0 .. t0+K)
-    float *ch = vh + (size_t)(K + 1) * S4;           // [K][S4]       m_c->v^(t0+1 .. t0+K)
+    float *cbar = vh + (size_t)(K + 1) * S4;         // [S4] adjoint of m_c->v^(t)
+    // coset loss scratch, [S4] float2 over vh[K] and cbar: the adjoint never
+    // reads m_v->c^(t0+K), and cbar is dead from the barrier that ends one
+    // adjoint iteration's check step until step A of the next writes it
+    float2 *ub2 = reinterpret_cast<float2 *>(vh + (size_t)K * S4);
+    float *ch = cbar + S4;                           // [K][S4]       m_c->v^(t0+1 .. t0+K)
     float *Qh = ch + (size_t)K * S4;                 // [(K+1)][3Np]  Q^(t0 .. t0+K)
     float *gh = Qh + (size_t)(K + 1) * 3 * Np;       // [(K+1)][3Np]  g^(t0 .. t0+K) (Momentum only)
     float *vbar = gh + (MODEL == kMomentum ? (size_t)(K + 1) * 3 * Np : 0);  // [S4] adjoint of m_v->c^(t)
-    float *cbar = vbar + S4;                         // [S4] adjoint of m_c->v^(t)
-    float *red = cbar + S4;                          // [64]
+    float *red = vbar + S4;                          // [64]
     float2 *red2 = reinterpret_cast<float2 *>(red);
     const int x = threadIdx.x, shot = blockIdx.x;
     Adj d;
@@ -828,9 +831,8 @@ int bpq_train_backward(const bpq_tanner *t, int model, const uint32_t *syn_dev, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int K = a.K, Np = a.n_pad, S4 = 4 * Np + 4;
     const size_t hist = (size_t)(K + 1) * 3 * Np * (mom ? 2 : 1);
-    const bool coset = a.loss_kind == BPQ_TRAIN_LOSS_COSET;
-    const size_t smem = sizeof(float) * ((coset ? 2 * (size_t)S4 : 0) + 3 * Np + (size_t)(K + 1) * S4 +
-                                         (size_t)K * S4 + hist + 2 * S4 + 64);
+    // the coset loss's scratch lives in dead parts of the history (no extra bytes)
+    const size_t smem = sizeof(float) * (3 * Np + (size_t)(K + 1) * S4 + (size_t)K * S4 + hist + 2 * S4 + 64);
     if (smem > 227 * 1024) return fail(BPQ_EINVAL, "checkpoint interval too long for shared memory");
     void (*fn)(const bpq::tr::TrainArgs) = mom ? bpq::tr::train_backward_kernel<bpq::tr::kMomentum>
                                                : bpq::tr::train_backward_kernel<bpq::tr::kEWAInit>;
