@@ -122,7 +122,7 @@ def test_training_lowers_the_loss(bpq):
         with torch.no_grad():
             a.clamp_(0.0, 1.0)
             b.clamp_(0.0, 0.95)
-        losses.append(float(L))
+        losses.append(L.item())
     assert losses[-1] < losses[0]
 
 
