@@ -426,10 +426,12 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
  * which the host saw the request finish; latency = done_s - arrival_s.
  * lanes_used (may be NULL): the largest number of lanes busy at once (slot
  * server: its CTAs).  Slot server: when est_host, conv_host and iters_host
- * are page-locked (cudaHostAlloc or cudaHostRegister) and every est_off is a
- * multiple of 16, the kernel writes each result into them directly and the
- * host only reads the completion queue; otherwise results pass through the
- * rings and the host copies them out.  Returns when every request is done.
+ * are page-locked (cudaHostAlloc or cudaHostRegister), est_host starts on a
+ * 16-byte boundary and every est_off is a multiple of 16, the kernel writes
+ * each result into them directly and the host only reads the completion
+ * queue; otherwise results pass through the rings and the host copies them
+ * out.  Returns when every request is done; on an error it first stops the
+ * serving kernel, so nothing is written to the outputs after it returns.
  * Errors: EINVAL (NULL arrays, a code index out of range, decreasing
  * arrival times, an estimate outside est_bytes), ECUDA. */
 int bpq_server_replay(bpq_server *s, int n_req, const int *code, const double *arrival_s, const uint32_t *syn_host,

@@ -195,17 +195,20 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
                 uint8_t *conv_host, uint8_t *iters_host, double *done_s, int *lanes_used) {
     SlotRings &R = s->ring;
     const int n_codes = (int)s->codes.size(), cap = R.cap;
-    // direct mode: with page-locked outputs and 16-byte aligned estimate
-    // offsets the kernel writes every result where it belongs, and the host
-    // only reads the completion queue; otherwise results go through the rings
+    // direct mode: with page-locked outputs and 16-byte aligned estimates
+    // (the buffer's start, host and device address, and every offset; the
+    // kernel stores them in 16-byte chunks) the kernel writes every result
+    // where it belongs, and the host only reads the completion queue;
+    // otherwise results go through the rings
     bpq::ServeOut out{nullptr, nullptr, nullptr};
-    bool aligned = n_req > 0;
+    bool aligned = n_req > 0 && (reinterpret_cast<uintptr_t>(est_host) & 15u) == 0;
     for (int r = 0; r < n_req && aligned; ++r) aligned = (est_off[r] & 15) == 0;
     if (aligned) {
         out.est = pinned_device_pointer(est_host, est_bytes);
         out.conv = pinned_device_pointer(conv_host, (size_t)n_req);
         out.iters = pinned_device_pointer(iters_host, (size_t)n_req);
-        if (!out.est || !out.conv || !out.iters) out = bpq::ServeOut{nullptr, nullptr, nullptr};
+        if (!out.est || !out.conv || !out.iters || (reinterpret_cast<uintptr_t>(out.est) & 15u) != 0)
+            out = bpq::ServeOut{nullptr, nullptr, nullptr};
     }
     const bool direct = out.est != nullptr;
     // a fresh stream of requests: claim counters, completion count, counters,
@@ -229,6 +232,13 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
 
     const auto t0 = steady::now();
     auto now = [&]() { return std::chrono::duration<double>(steady::now() - t0).count(); };
+    // an error inside the loop first closes the stream and waits for the
+    // kernel, so that it writes nothing to the caller's buffers afterwards
+    auto stop = [&](int code_) {
+        __atomic_store_n(R.closed, 1u, __ATOMIC_RELEASE);
+        cudaStreamSynchronize(R.st);
+        return code_;
+    };
     // host bookkeeping in flat arrays: request in each slot (-1 free)
     std::vector<uint32_t> admitted(n_codes, 0);
     std::vector<int> req_of((size_t)n_codes * cap, -1);
@@ -331,17 +341,17 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
             if (tdone < 0) tdone = now();
             const int c = (int)q->y;
             const uint32_t k = q->z, cw = q->w;
-            if (c < 0 || c >= n_codes) return fail(BPQ_ECUDA, "server: completion of an unknown code");
+            if (c < 0 || c >= n_codes) return stop(fail(BPQ_ECUDA, "server: completion of an unknown code"));
             int r;
             if (direct) {
                 // the entry names the request; its outputs are in place
                 r = (int)k;
-                if (r < 0 || r >= n_req) return fail(BPQ_ECUDA, "server: completion of an unknown request");
+                if (r < 0 || r >= n_req) return stop(fail(BPQ_ECUDA, "server: completion of an unknown request"));
             } else {
                 const int slot = (int)(k % (uint32_t)cap);
                 int &occ = req_of[(size_t)c * cap + slot];
                 r = occ;
-                if (r < 0) return fail(BPQ_ECUDA, "server: completion of a request that is not in flight");
+                if (r < 0) return stop(fail(BPQ_ECUDA, "server: completion of a request that is not in flight"));
                 std::memcpy(est_host + est_off[r], R.est[c] + (size_t)slot * N16[c], N[c]);
                 conv_host[r] = (uint8_t)(cw & 0xFFu);
                 iters_host[r] = (uint8_t)((cw >> 8) & 0xFFu);
@@ -369,15 +379,15 @@ int slot_replay(bpq_server *s, int n_req, const int *code, const double *arrival
         if (q == cudaSuccess && completed < n_req) {
             uint32_t st3[3];
             rc = slot_status(s, st3);
-            if (rc) return rc;
-            if (st3[1]) return fail(BPQ_ECUDA, "server: a bounded wait inside the kernel gave up");
+            if (rc) return stop(rc);
+            if (st3[1]) return stop(fail(BPQ_ECUDA, "server: a bounded wait inside the kernel gave up"));
             // completions written just before the kernel returned are read first
             uint4 *qq = R.cq + (cq_read % R.cq_len);
             if (__atomic_load_n(&qq->x, __ATOMIC_ACQUIRE) == cq_read + 1u) continue;
             rc = slot_launch(s);
-            if (rc) return rc;
+            if (rc) return stop(rc);
         } else if (q != cudaSuccess && q != cudaErrorNotReady) {
-            return fail(BPQ_ECUDA, std::string("server kernel: ") + cudaGetErrorString(q));
+            return stop(fail(BPQ_ECUDA, std::string("server kernel: ") + cudaGetErrorString(q)));
         }
     }
     // every request is done: close the stream; the kernel's CTAs return

@@ -115,6 +115,49 @@ def test_slot_server_direct_and_ring_outputs_agree(bpq):
     check_alone(bpq, codes, priors, code_of, syn_list, *direct[:3])
 
 
+def test_slot_server_unaligned_outputs_use_the_rings(bpq):
+    """Page-locked outputs whose estimate buffer starts one byte past a
+    16-byte boundary, at offsets that are multiples of 16: the kernel's
+    16-byte stores there would be misaligned, so the server takes the rings
+    (the host copies the results out).  Called through the C ABI, since the
+    binding allocates aligned buffers; the results equal the in-place ones."""
+    import ctypes
+
+    from paper_2407_11523_gb300 import _binding as B
+
+    codes = [bpq.Tanner("planar", 9), bpq.Tanner("xzzx", 5)]
+    ch = oracle.depolarizing(0.05)
+    priors = [bpq.prior_tensor(t, *ch) for t in codes]
+    srv = bpq.Server(codes, priors, "ewainit", max_iter=100, mode="slots", slots_per_code=32)
+    code_of, arrival, syn_list = make_trace(bpq, codes, 600, 2e5, seed=36)
+    ref = srv.replay(code_of, arrival, syn_list, pinned=True)
+    R = code_of.size
+    Ns = [codes[c].N for c in code_of]
+    stride = [(n + 15) & ~15 for n in Ns]
+    est_off = np.zeros(R, dtype=np.int64)
+    est_off[1:] = np.cumsum(stride)[:-1]
+    syn_off = np.zeros(R, dtype=np.int64)
+    syn_off[1:] = np.cumsum([len(x) for x in syn_list])[:-1]
+    syn = np.ascontiguousarray(np.concatenate(syn_list).astype(np.uint32))
+    n_est = int(sum(stride))
+    base = torch.zeros(n_est + 16, dtype=torch.uint8, pin_memory=True).numpy()
+    assert base.ctypes.data % 16 == 0
+    est = base[1:1 + n_est]
+    conv = torch.zeros(R, dtype=torch.uint8, pin_memory=True).numpy()
+    iters = torch.zeros(R, dtype=torch.uint8, pin_memory=True).numpy()
+    done = np.zeros(R, dtype=np.float64)
+    code32 = np.ascontiguousarray(code_of, dtype=np.int32)
+    arr = np.ascontiguousarray(arrival, dtype=np.float64)
+    used = ctypes.c_int()
+    rc = B.lib().bpq_server_replay(srv._h, R, B._ptr(code32), B._ptr(arr), B._ptr(syn), B._ptr(syn_off), B._ptr(est),
+                                   B._ptr(est_off), n_est, B._ptr(conv), B._ptr(iters), B._ptr(done),
+                                   ctypes.byref(used))
+    assert rc == 0, B.lib().bpq_last_error()
+    for r in range(R):
+        assert (est[est_off[r]:est_off[r] + Ns[r]] == ref[0][r]).all()
+    assert (conv == ref[1]).all() and (iters == ref[2]).all()
+
+
 def test_slot_server_relaunches_after_idle(bpq):
     """With a 50 us idle limit and 3 ms gaps between bursts, the serving
     kernel returns (a bounded wait, status 2) between bursts and the host
