@@ -11,6 +11,10 @@
  *  - Pointers named *_dev are device pointers owned by the caller (for
  *    example torch tensors' data_ptr()); pointers named *_host are host
  *    pointers owned by the caller.  The library never frees them.
+ *  - Alignment: device buffers passed as void * (workspaces, dev_buf,
+ *    dev_mem) start on a 16-byte boundary (cudaMalloc and torch give 256),
+ *    and uint32 / float arrays on a 4-byte one; an entry point refuses a
+ *    misaligned base with BPQ_EINVAL before any device access.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  GPU entry
  *    points only enqueue work on it and return; they do not synchronize,
  *    except where a function says otherwise.

@@ -230,6 +230,9 @@ int fill_decode_args(const bpq_tanner *t, const uint32_t *syn, const float *prio
     if (B < 0) return fail(BPQ_EINVAL, "B < 0");
     if (max_iter < 1 || max_iter > 255) return fail(BPQ_EINVAL, "max_iter must be in [1, 255]");
     if (B > 0 && (!syn || !prior || !work)) return fail(BPQ_EINVAL, "NULL input or workspace");
+    if (misaligned(work, kBufferAlign)) return fail(BPQ_EINVAL, "workspace not 16-byte aligned");
+    if (misaligned(syn, kWordAlign) || misaligned(prior, kWordAlign))
+        return fail(BPQ_EINVAL, "syndromes or priors not 4-byte aligned");
     std::memset(&a, 0, sizeof a);
     a.split = t->full ? 2 : t->split ? 1 : 0;
     a.table = t->split ? t->d_table_split : t->d_table;
@@ -309,6 +312,7 @@ int decode_host_impl(const bpq_tanner *t, const uint32_t *syn_host, const float 
     if (B == 0) return BPQ_OK;
     if (!syn_host || !prior_host || !est_host || !conv_host || !iters_host || !dev_buf)
         return fail(BPQ_EINVAL, "NULL argument");
+    if (bpq::misaligned(dev_buf, bpq::kBufferAlign)) return fail(BPQ_EINVAL, "device buffer not 16-byte aligned");
     if (dev_buf_bytes < bpq_decode_host_bytes(t, B)) return fail(BPQ_EINVAL, "device buffer too small");
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t W = (t->M + 31) / 32, N = (size_t)t->N;

@@ -73,6 +73,7 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
     if (variant < BPQ_PLAIN || variant > BPQ_EWAINIT)
         return fail(BPQ_EINVAL, "the batched kernel takes plain, Momentum, AdaGrad or EWAInit BP");
     if (!work_dev) return fail(BPQ_EINVAL, "NULL workspace");
+    if (bpq::misaligned(work_dev, bpq::kBufferAlign)) return fail(BPQ_EINVAL, "workspace not 16-byte aligned");
     const int device = items[0].tanner ? items[0].tanner->device : -1;
     long total = 0;
     for (int g = 0; g < n_items; ++g) {
@@ -83,6 +84,8 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
         if (items[g].B > 0 && (!items[g].syn_dev || !items[g].prior_dev || !items[g].est_dev ||
                                !items[g].conv_dev || !items[g].iters_dev))
             return fail(BPQ_EINVAL, "NULL input or output in a batch item");
+        if (bpq::misaligned(items[g].syn_dev, bpq::kWordAlign) || bpq::misaligned(items[g].prior_dev, bpq::kWordAlign))
+            return fail(BPQ_EINVAL, "a batch item's syndromes or prior not 4-byte aligned");
         total += items[g].B;
     }
     if (work_bytes < bpq_batch_workspace_bytes(n_items)) return fail(BPQ_EINVAL, "batch workspace too small");

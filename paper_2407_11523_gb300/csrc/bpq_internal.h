@@ -21,6 +21,17 @@ constexpr size_t kWorkspaceBytes = 256;  // [0] next shot, [1] device error word
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 
+// Alignment the entry points require of caller buffers: device buffers passed
+// as void * (workspaces, the host path's buffer, a server's device memory) are
+// cut into 32-bit words and descriptors with 64-bit fields, which kernels may
+// copy in 16-byte bulk copies; syndromes and priors are read as 32-bit words.
+// A base off these boundaries would make the device accesses misaligned, so
+// the entry points refuse it (BPQ_EINVAL) instead.
+constexpr size_t kBufferAlign = 16, kWordAlign = 4;
+inline bool misaligned(const void *p, size_t align) {
+    return (reinterpret_cast<uintptr_t>(p) & (align - 1)) != 0;
+}
+
 // One qubit of the serial schedule's sweep (48 bytes, 16-byte aligned); the
 // serial table lists them level by level (see serial.cu).  Message slots
 // index the kernel's per-shot message array: every edge has one slot, laid

@@ -421,6 +421,7 @@ int bpq_server_create(const bpq_tanner *const *codes, const float *const *priors
     if (n_lanes < 1 || n_lanes > 64 || max_batch < 1) return fail(BPQ_EINVAL, "bad lane count or batch size");
     if (dev_bytes < bpq_server_device_bytes(codes, n_codes, n_lanes, max_batch) || !dev_mem)
         return fail(BPQ_EINVAL, "device memory budget too small");
+    if (bpq::misaligned(dev_mem, bpq::kBufferAlign)) return fail(BPQ_EINVAL, "device memory not 16-byte aligned");
     const int device = codes[0] ? codes[0]->device : -1;
     bpq_server *s = new (std::nothrow) bpq_server();
     if (!s) return fail(BPQ_ENOMEM, "allocation failed");
@@ -666,6 +667,7 @@ int bpq_server_create_slots(const bpq_tanner *const *codes, const float *const *
     if (slots_per_code < 1 || slots_per_code > (1 << 20)) return fail(BPQ_EINVAL, "slots per code must be in [1, 2^20]");
     if (idle_timeout_us < 1) return fail(BPQ_EINVAL, "idle timeout must be at least 1 us");
     if (!dev_mem || dev_bytes < slot_device_bytes(n_codes)) return fail(BPQ_EINVAL, "device memory budget too small");
+    if (bpq::misaligned(dev_mem, bpq::kBufferAlign)) return fail(BPQ_EINVAL, "device memory not 16-byte aligned");
     const int device = codes[0] ? codes[0]->device : -1;
     bpq_server *s = new (std::nothrow) bpq_server();
     if (!s) return fail(BPQ_ENOMEM, "allocation failed");

@@ -723,6 +723,10 @@ int fill(const bpq_tanner *t, int model, const uint32_t *syn, const uint8_t *err
     if (model != kEWAInit && model != kMomentum) return fail(BPQ_EINVAL, "unknown training model");
     if (B < 1 || T < 1 || T > 255 || K < 1) return fail(BPQ_EINVAL, "bad B, T or checkpoint interval");
     if (!syn || !err || !prior || !alpha || !beta || !w || !work) return fail(BPQ_EINVAL, "NULL argument");
+    if (misaligned(work, kBufferAlign)) return fail(BPQ_EINVAL, "workspace not 16-byte aligned");
+    if (misaligned(syn, kWordAlign) || misaligned(prior, kWordAlign) || misaligned(alpha, kWordAlign) ||
+        misaligned(beta, kWordAlign) || misaligned(w, kWordAlign) || (gamma && misaligned(gamma, kWordAlign)))
+        return fail(BPQ_EINVAL, "an input array not 4-byte aligned");
     if (model == kMomentum && !gamma) return fail(BPQ_EINVAL, "the Momentum model needs gamma");
     if (!(clip > 0.f)) return fail(BPQ_EINVAL, "msg_clip must be positive");
     const int kind = loss ? loss->kind : BPQ_TRAIN_LOSS_POSTERIOR;

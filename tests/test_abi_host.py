@@ -225,3 +225,24 @@ def test_serial_shots_per_warp_refusals(bpq):
     for k in (3, -1):
         with pytest.raises(bpq.BPQError):
             t.set_serial_shots_per_warp(k)
+
+
+def test_batch_plan_refuses_a_misaligned_workspace(bpq):
+    """A workspace that does not start on a 16-byte boundary is refused on the
+    host (BPQ_EINVAL) before the items are looked at; an aligned one goes on
+    to the next check (here: an item without an uploaded Tanner graph).  The
+    addresses are never dereferenced."""
+    from paper_2407_11523_gb300 import _binding as B
+
+    L = bpq.lib()
+    items = (B.BatchItem * 1)()
+    items[0] = B.BatchItem(None, None, None, 1, None, None, None)
+    p = bpq.make_params("ewainit")
+    out = ctypes.c_void_p()
+    rc = L.bpq_batch_plan(items, 1, 3, ctypes.byref(p), 100, ctypes.c_void_p(0x100008), 1 << 20, None,
+                          ctypes.byref(out))
+    assert rc == -1 and b"16-byte" in L.bpq_last_error()
+    rc = L.bpq_batch_plan(items, 1, 3, ctypes.byref(p), 100, ctypes.c_void_p(0x100000), 1 << 20, None,
+                          ctypes.byref(out))
+    assert rc == -4 and b"uploaded" in L.bpq_last_error()
+    assert not out.value

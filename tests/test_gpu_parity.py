@@ -619,3 +619,72 @@ def test_aewa_host_path_and_refusals(bpq):
         bpq.decode_trace(t, syn[:4].contiguous(), prior, "aewa", T=5)
     with pytest.raises(bpq.BPQError):
         bpq.BatchPlan([(t, syn, prior)], "aewa", max_iter=60)
+
+
+def test_misaligned_buffers_are_refused(bpq):
+    """Device buffers passed as void * that do not start on a 16-byte
+    boundary, and syndromes off a 4-byte one, are refused on the host with
+    BPQ_EINVAL before any device access: bpq_decode, bpq_decode_host, both
+    servers and training.  The context stays usable: an aligned decode then
+    equals a decode through the binding."""
+    import ctypes
+
+    from paper_2407_11523_gb300 import _binding as Bd
+
+    L = bpq.lib()
+    t = bpq.Tanner("planar", 5).upload()
+    ch = oracle.depolarizing(0.05)
+    prior = bpq.prior_tensor(t, *ch)
+    err, syn = bpq.sample(t, *ch, seed=5, shot0=0, B=64)
+    p = bpq.make_params("ewainit")
+    out = [torch.empty((64, t.N), dtype=torch.uint8, device="cuda"), torch.empty(64, dtype=torch.uint8, device="cuda"),
+           torch.empty(64, dtype=torch.uint8, device="cuda")]
+    work = torch.empty(1024, dtype=torch.uint8, device="cuda")
+
+    def decode(syn_ptr, work_ptr):
+        return L.bpq_decode(t.handle, ctypes.c_void_p(syn_ptr), Bd._ptr(prior), 3, ctypes.byref(p), 100, 64,
+                            Bd._ptr(out[0]), Bd._ptr(out[1]), Bd._ptr(out[2]), ctypes.c_void_p(work_ptr), None)
+
+    assert decode(syn.data_ptr(), work.data_ptr() + 8) == -1 and b"16-byte" in L.bpq_last_error()
+    assert decode(syn.data_ptr() + 2, work.data_ptr()) == -1 and b"4-byte" in L.bpq_last_error()
+
+    syn_h, pri_h = syn.cpu().pin_memory(), prior.cpu()
+    out_h = [torch.empty((64, t.N), dtype=torch.uint8), torch.empty(64, dtype=torch.uint8),
+             torch.empty(64, dtype=torch.uint8)]
+    need = L.bpq_decode_host_bytes(t.handle, 64)
+    dbuf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
+    rc = L.bpq_decode_host(t.handle, Bd._ptr(syn_h), Bd._ptr(pri_h), 3, ctypes.byref(p), 100, 64, Bd._ptr(out_h[0]),
+                           Bd._ptr(out_h[1]), Bd._ptr(out_h[2]), ctypes.c_void_p(dbuf.data_ptr() + 8), need, None)
+    assert rc == -1 and b"16-byte" in L.bpq_last_error()
+
+    harr = (ctypes.c_void_p * 1)(t.handle.value)
+    parr = (ctypes.c_void_p * 1)(prior.data_ptr())
+    h = ctypes.c_void_p()
+    nb = L.bpq_server_device_bytes(harr, 1, 1, 64)
+    mem = torch.empty(nb + 64, dtype=torch.uint8, device="cuda")
+    rc = L.bpq_server_create(harr, parr, 1, 3, ctypes.byref(p), 100, 1, 64, ctypes.c_void_p(mem.data_ptr() + 8), nb,
+                             ctypes.byref(h))
+    assert rc == -1 and b"16-byte" in L.bpq_last_error() and not h.value
+    nb = L.bpq_server_slot_device_bytes(1)
+    mem = torch.empty(nb + 64, dtype=torch.uint8, device="cuda")
+    rc = L.bpq_server_create_slots(harr, parr, 1, 3, ctypes.byref(p), 100, 32, 1000,
+                                   ctypes.c_void_p(mem.data_ptr() + 8), nb, ctypes.byref(h))
+    assert rc == -1 and b"16-byte" in L.bpq_last_error() and not h.value
+
+    T, K = 5, 5
+    a = torch.full((T,), 0.5, device="cuda")
+    b = torch.zeros(T, device="cuda")
+    w = torch.ones(t.E, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    nbytes = L.bpq_train_workspace_bytes(t.handle, 0, 64, T, K)
+    tw = torch.empty(nbytes + 64, dtype=torch.uint8, device="cuda")
+    rc = L.bpq_train_forward(t.handle, 0, Bd._ptr(syn), Bd._ptr(err), Bd._ptr(prior), 64, T, K, Bd._ptr(a),
+                             Bd._ptr(b), None, Bd._ptr(w), 30.0, None, Bd._ptr(loss), None,
+                             ctypes.c_void_p(tw.data_ptr() + 8), nbytes, None)
+    assert rc == -1 and b"16-byte" in L.bpq_last_error()
+
+    assert decode(syn.data_ptr(), work.data_ptr()) == 0
+    ref = bpq.decode(t, syn, prior, "ewainit", params=p, max_iter=100)
+    torch.cuda.synchronize()
+    for x, y in zip(out, ref):
+        assert torch.equal(x, y)

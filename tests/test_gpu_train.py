@@ -52,7 +52,7 @@ def test_loss_matches_oracle(bpq, T, K):
     H, s, e, pri = oracle_inputs(t, err, syn, ch)
     Lr = float(unrolled.loss(unrolled.forward(unrolled.Graph(H), s, pri, torch.tensor(a), torch.tensor(b),
                                               torch.tensor(w), T), e))
-    assert float(L) == pytest.approx(Lr, rel=2e-4)
+    assert L.item() == pytest.approx(Lr, rel=2e-4)
 
 
 @pytest.mark.parametrize("T", [6, 12])
@@ -157,7 +157,7 @@ def test_momentum_gradients_match_oracle_and_finite_differences(bpq, T):
     ga, gb, gw, gg = (x.grad.detach().cpu().numpy().astype(np.float64) for x in ts)
     H, s, e, pri = oracle_inputs(t, err, syn, ch)
     Lr, ra, rb, rw, rg = unrolled.loss_and_grads(H, s, e, pri, a, b, w, T, model="momentum", gamma=gm)
-    assert float(L) == pytest.approx(Lr, rel=2e-4)
+    assert L.item() == pytest.approx(Lr, rel=2e-4)
     for g, r in ((ga, ra), (gb, rb), (gw, rw), (gg, rg)):
         scale = np.abs(r).max()
         assert np.abs(g - r).max() <= 2e-3 * scale + 1e-7, (np.abs(g - r).max(), scale)
@@ -211,7 +211,7 @@ def test_coset_loss_matches_oracle(bpq, model, T, K):
     Qs = unrolled.forward(unrolled.Graph(H), s, pri, torch.tensor(a), torch.tensor(b), torch.tensor(w), T,
                           model=model, gamma=torch.tensor(gm) if model == "momentum" else None, every=True)
     Lr = float(unrolled.coset_loss(Qs, H, s, e, Lg))
-    assert float(L) == pytest.approx(Lr, rel=2e-4)
+    assert L.item() == pytest.approx(Lr, rel=2e-4)
 
 
 @pytest.mark.parametrize("model", ["ewainit", "momentum"])
@@ -231,7 +231,7 @@ def test_coset_gradients_match_oracle_and_finite_differences(bpq, model):
     got = [x.grad.detach().cpu().numpy().astype(np.float64) for x in ts]
     ref = unrolled.loss_and_grads(H, s, e, pri, a, b, w, T, model=model, gamma=gm if model == "momentum" else None,
                                   kind="coset", logicals=Lg)
-    assert float(L) == pytest.approx(ref[0], rel=2e-4)
+    assert L.item() == pytest.approx(ref[0], rel=2e-4)
     for g, r in zip(got, ref[1:]):
         scale = np.abs(r).max()
         assert np.abs(g - r).max() <= 2e-3 * scale + 1e-7, (np.abs(g - r).max(), scale)
