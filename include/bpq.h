@@ -186,7 +186,10 @@ int bpq_decode_status(const void *work_dev, void *stream, int *device_error);
  * alternately on `stream` and on a library stream (so that one chunk's last
  * shots overlap the next chunk), and the copies run on two more library
  * streams, all three per device, created on first use and kept (calls from
- * several host threads on one device share them). */
+ * several host threads on one device share them).  Errors: as bpq_decode,
+ * plus EINVAL (NULL host buffers, dev_buf smaller than
+ * bpq_decode_host_bytes(t, B) or not 16-byte aligned) and ECUDA (a copy or
+ * the synchronization failed). */
 size_t bpq_decode_host_bytes(const bpq_tanner *t, int B);
 int bpq_decode_host(const bpq_tanner *t, const uint32_t *syn_host, const float *prior_host,
                     int variant, const bpq_params *params, int max_iter, int B, uint8_t *est_host,
@@ -224,7 +227,8 @@ int bpq_decode_host_noalloc_max_shots(const bpq_tanner *t);
  * iterations without the stopping rule and writes, in check-major edge
  * order (bpq_tanner_export), m_v2c_dev [B][T+1][E] (t = 0 is eq. (init)),
  * m_c2v_dev [B][T][E], Q_dev [B][T][N][3] and dec_dev [B][T][N].  Any
- * record pointer may be NULL.  T in [1, 255]. */
+ * record pointer may be NULL.  T in [1, 255].  Errors: as bpq_decode
+ * (AEWA-BP has no trace: EINVAL). */
 int bpq_decode_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev,
                      int variant, const bpq_params *params, int T, int B, float *m_v2c_dev,
                      float *m_c2v_dev, float *Q_dev, uint8_t *dec_dev, void *work_dev, void *stream);
@@ -277,7 +281,9 @@ int bpq_set_debug_checks(bpq_tanner *t, int on);
  * CTA - and stores the fastest in the handle (as bpq_set_launch and
  * bpq_set_shots_per_thread would).  Synchronizes `stream`; the outputs are
  * those of the last trial.  Reports the chosen shape and its time per
- * launch (any output pointer may be NULL). */
+ * launch (any output pointer may be NULL).  Errors: as bpq_decode, plus
+ * EINVAL when B < 1 or no shape fits the code; on an error the handle keeps
+ * its previous shape. */
 int bpq_autotune(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
                  const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
                  uint8_t *iters_dev, void *work_dev, void *stream, int *threads_per_shot, int *shots_per_cta,
@@ -321,7 +327,7 @@ int bpq_set_serial_shots_per_warp(bpq_tanner *t, int shots_per_warp);
 /* Per-sweep record of the serial schedule, in bpq_decode_trace's layout:
  * exactly T sweeps, no stopping rule; m_v2c_dev [B][T+1][E] holds each
  * edge's v->c message as sent in that sweep, m_c2v_dev [B][T][E] the c->v
- * message its qubit took. */
+ * message its qubit took.  Errors: as bpq_decode_serial. */
 int bpq_decode_serial_trace(const bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
                             const bpq_params *params, int T, int B, float *m_v2c_dev, float *m_c2v_dev, float *Q_dev,
                             uint8_t *dec_dev, void *work_dev, void *stream);
@@ -364,11 +370,13 @@ int bpq_batch_plan(const bpq_batch_item *items, int n_items, int variant, const 
 
 /* Enqueue one run of the plan on `stream` (a counter reset and one kernel
  * launch; no host synchronization and no allocation, so the call can be
- * captured in a CUDA graph).  Runs of one plan must not overlap. */
+ * captured in a CUDA graph).  Runs of one plan must not overlap.  Errors:
+ * EINVAL (NULL plan), ECUDA (the launch failed). */
 int bpq_batch_launch(const bpq_batch *b, void *stream);
 
 /* ctas: CTAs per launch; items: n_items; npt_max: the largest nodes per
- * thread of an item; shots: total shots.  Any pointer may be NULL. */
+ * thread of an item; shots: total shots.  Any pointer may be NULL.
+ * Errors: EINVAL (NULL plan). */
 int bpq_batch_info(const bpq_batch *b, int *ctas, int *items, int *npt_max, long *shots);
 void bpq_batch_free(bpq_batch *b);
 
@@ -393,7 +401,8 @@ int bpq_get_batch_launch(const bpq_tanner *t, int variant, int *threads_per_shot
  * bpq_batch_workspace_bytes(1) bytes) with one and with two nodes per
  * thread, and stores the faster in the handle.  Synchronizes `stream`; the
  * outputs are those of the last trial.  Reports the choice and its time per
- * launch (any output pointer may be NULL). */
+ * launch (any output pointer may be NULL).  Errors: as bpq_batch_plan and
+ * bpq_batch_launch (a workspace below bpq_batch_workspace_bytes(1): EINVAL). */
 int bpq_autotune_batch(bpq_tanner *t, const uint32_t *syn_dev, const float *prior_dev, int variant,
                        const bpq_params *params, int max_iter, int B, uint8_t *est_dev, uint8_t *conv_dev,
                        uint8_t *iters_dev, void *work_dev, size_t work_bytes, void *stream,
